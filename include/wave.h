@@ -1,0 +1,228 @@
+/*
+ * wave.h -- C ABI of libwave.so, a time-tiled 3D acoustic wave stencil for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The library advances the damped acoustic wave equation
+ *     m u_tt + d u_t = Lap u + q
+ * with second-order leapfrog in time and a centred space stencil of order SO
+ * (4, 8 or 16), i.e. the update printed in McCormick 2017, "Applying the
+ * Polyhedral Model to Tile Loops in Devito", Fig. acoustic_devito:
+ *     u[t+1] = ((dt d - 2m) u[t-1] + 4m u[t] + 2dt^2 (L_h u[t] + q)) / (dt d + 2m).
+ * It runs the update either one step per pass over HBM (the plain method) or
+ * T steps per pass (time tiling, Chapter "Time-Tiling": the time loop moved
+ * inside the spatial tile loops, spatial loops skewed by SO/2 per step).
+ *
+ * Units: spacing in metres, dt in milliseconds, velocity in km/s, so
+ * m = 1/v^2 is in (ms/m)^2 and v dt / h is dimensionless.
+ *
+ * Layout of every 3D array crossing this ABI: float32, [nx][ny][nz]
+ * row-major, z fastest (the paper's u[time][x][y][z] without the time index,
+ * Fig. acoustic_devito).  Grid index (i, j, k) sits at (i hx, j hy, k hz)
+ * metres.  Points outside the grid are zero (a zero Dirichlet ghost layer of
+ * width SO/2 that is never written, Section "Simulation").
+ *
+ * Pointers: "device" pointers must be CUDA device (or managed) memory on the
+ * plan's device; "host" pointers are ordinary host memory.  The caller owns
+ * every pointer it passes; the plan copies what it keeps (the model, tap
+ * lists) and owns its wavefield buffers.  Calls are ordered on the plan's
+ * stream (wave_options.stream; 0 = legacy default stream).
+ *
+ * Errors: every call returns a wave_status; nothing throws across the ABI.
+ * On failure, wave_last_error() returns a message for the calling thread.
+ * A failed call leaves the plan usable unless it returns WAVE_ERR_CUDA.
+ */
+#ifndef WAVE_H
+#define WAVE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WAVE_OK = 0,
+    WAVE_ERR_ARG = 1,     /* invalid argument (null, size, SO, range)            */
+    WAVE_ERR_CFL = 2,     /* dt above the leapfrog stability limit               */
+    WAVE_ERR_OOM = 3,     /* device or host allocation failed                    */
+    WAVE_ERR_CUDA = 4,    /* a CUDA call failed; the plan should be destroyed    */
+    WAVE_ERR_TIMEOUT = 5, /* a bounded device-side wait gave up (see wave.h top) */
+    WAVE_ERR_STATE = 6    /* call out of order (e.g. no sources set)             */
+} wave_status;
+
+typedef struct wave_plan_s* wave_plan_t;
+
+/* Tiling of one pass (a "tile schedule"):
+ *   T  : time steps per pass over HBM (1 = the plain one-step method);
+ *   by : output tile extent along y (points);
+ *   bz : output tile extent along z (points, multiple of 4);
+ *   xc : extent along x of the slab one thread block streams through.
+ * Every field 0 = let the library choose (autotuner or built-in default). */
+typedef struct {
+    int T, by, bz, xc;
+} wave_tiling;
+
+typedef struct {
+    int sponge_width;  /* absorbing layer width in cells (default 10, 0 = none)  */
+    int sponge_faces;  /* bit f set = face f absorbs, faces x-,x+,y-,y+,z-,z+;    */
+                       /* default 0x2F: all but z- (z = 0 is the free surface)   */
+    double vmax;       /* km/s, sets the sponge strength (default: from m)       */
+    void* stream;      /* cudaStream_t for every call on the plan (default 0)    */
+    wave_tiling tiling;/* forced tiling of the forward passes (0s = choose)      */
+    int autotune;      /* 1 = time candidate tilings on the GPU at plan creation,*/
+                       /* 0 = built-in default (the default)                     */
+    int device;        /* CUDA device ordinal (default: current device)          */
+} wave_options;
+
+/* Fill *opt with the defaults listed above.  Returns WAVE_ERR_ARG on NULL. */
+wave_status wave_options_default(wave_options* opt);
+
+/* Centred second-derivative FD weights of accuracy order `so` (2..16, even) on
+ * unit spacing, a[0] (centre) .. a[so/2], as exact rationals rounded to double:
+ *   a_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!),  a_0 = -2 sum_k a_k.
+ * Fig. acoustic_devito prints these for SO 8 times 2dt^2/h^2.
+ * `a` is host memory of so/2 + 1 doubles.  Host only, no GPU needed. */
+wave_status wave_fd_weights(int so, double* a);
+
+/* Largest stable dt (ms) of the leapfrog update for velocity vmax (km/s):
+ * 2 / (vmax sqrt(rho sum_a 1/h_a^2)), rho = |a_0| + 2 sum_k |a_k|.
+ * spacing: host [3] metres.  Host only. */
+wave_status wave_cfl_limit(int so, const double spacing[3], double vmax, double* dt_max);
+
+/* Create a plan: validates the problem, builds the FD coefficients, checks
+ * the CFL limit (WAVE_ERR_CFL), allocates the wavefield buffers and converts
+ * the model.  grid: host [3] = nx, ny, nz (each >= so + 1); spacing: host [3]
+ * metres; so in {4, 8, 16}; dt > 0 in ms; nt >= 0 time steps;
+ * m: device [nx][ny][nz] squared slowness (copied, not kept); opt may be NULL.
+ * The plan is bound to the device current at the call (or opt->device). */
+wave_status wave_plan_create(wave_plan_t* out, const int grid[3], const double spacing[3], int so,
+                             double dt, int nt, const float* m, const wave_options* opt);
+
+/* Replace the model (device [nx][ny][nz], copied).  Recomputes the per-point
+ * coefficients; sources and receivers stay. */
+wave_status wave_set_model(wave_plan_t plan, const float* m);
+
+/* Point sources: xyz host [nsrc][3] metres, injected through trilinear
+ * weights as a term of the discrete equation (L_h u -> L_h u + sum w q);
+ * wavelet device [nt][nsrc] (copied).  Update n injects row n.  nsrc = 0
+ * clears the sources.  The paper removes its source before tiling (Section
+ * "Functional Correctness"); here it is fused into every pass. */
+wave_status wave_set_sources(wave_plan_t plan, int nsrc, const double* xyz, const float* wavelet);
+
+/* Receivers: xyz host [nrec][3] metres; trace n of receiver j is the
+ * trilinear interpolation of u^{n+1} (the field produced by update n).
+ * nrec = 0 clears them. */
+wave_status wave_set_receivers(wave_plan_t plan, int nrec, const double* xyz);
+
+/* Force the tiling of the forward passes (see wave_tiling); T = 1 selects the
+ * plain one-step kernel.  Fields of 0 are chosen by the library.  Rejects a
+ * schedule the tile-legality scheduler does not accept (WAVE_ERR_ARG). */
+wave_status wave_set_tiling(wave_plan_t plan, const wave_tiling* tiling);
+
+/* The tiling the forward passes use now (after defaults / autotuning). */
+wave_status wave_get_tiling(wave_plan_t plan, wave_tiling* tiling);
+
+/* Time candidate tilings on the GPU for this plan (T = 1..Tmax, several tile
+ * shapes and slab lengths) with `passes` timed passes each, and keep the
+ * fastest in point-steps per second (T = 1 may win: the paper's remark that
+ * time tiling is only worthwhile when the loop is memory-bound).  T_only > 0
+ * restricts the sweep to that T.  The plan's wavefields are scratch during
+ * the sweep.  cand / ms_per_step: host arrays of up to `cap` entries (may be
+ * NULL) receiving every timed candidate and its milliseconds per time step;
+ * *ncand (may be NULL) receives how many were timed. */
+wave_status wave_autotune(wave_plan_t plan, int passes, int T_only, wave_tiling* cand, double* ms_per_step,
+                          int cap, int* ncand);
+
+/* Forward modelling of nt steps from u^{-1}, u^0.
+ * u_init: device [2][nx][ny][nz] = (u^{-1}, u^0), or NULL for zero fields.
+ * rec_out: device [nt][nrec] traces, may be NULL when nrec = 0.
+ * u_final: device [2][nx][ny][nz] receiving (u^{nt-1}, u^{nt}), may be NULL.
+ * Synchronises the plan's stream at the end to report device-side timeouts
+ * (WAVE_ERR_TIMEOUT). */
+wave_status wave_forward(wave_plan_t plan, const float* u_init, float* rec_out, float* u_final);
+
+/* The same as wave_forward with every array in host memory (copies inside). */
+wave_status wave_forward_host(wave_plan_t plan, const float* m_host, const float* wavelet_host,
+                              float* rec_host);
+
+/* Adjoint modelling: the transpose of the linear map wavelet -> traces of
+ * wave_forward (zero initial fields).  rec_resid: device [nt][nrec] is
+ * injected at the receivers backwards in time; src_out: device [nt][nsrc]
+ * receives the adjoint field sampled at the sources.  Uses the same update
+ * (L_h symmetric, damping diagonal), with receivers and sources swapping
+ * roles; see the gradient below. */
+wave_status wave_adjoint(wave_plan_t plan, const float* rec_resid, float* src_out);
+
+/* Misfit J = 1/2 sum (rec - d_obs)^2 of the plan's sources and receivers and
+ * its gradient with respect to m (adjoint state):
+ *   dJ/dm = - sum_n mu^{n+1} (u^{n+1} - 2u^n + u^{n-1}) / dt^2,
+ * mu the adjoint field driven by rec - d_obs.  d_obs: device [nt][nrec];
+ * grad_m: device [nx][ny][nz]; misfit: host double (may be NULL).
+ * checkpoint_every = K > 0 stores (u^{n-1}, u^n) every K steps and recomputes
+ * each K-step segment forward before its adjoint sweep (memory ~ (nt/K + K)
+ * fields); K = 0 stores every level when it fits in device memory. */
+wave_status wave_gradient(wave_plan_t plan, const float* d_obs, float* grad_m, double* misfit,
+                          int checkpoint_every);
+
+/* Measurement hook.  With enable = 1 every pass kernel the plan launches is
+ * bracketed by a pair of CUDA events recorded on the plan's stream, so the
+ * caller can read the kernel's own device time without a profiler.
+ * Counting of launched kernels is always on. */
+wave_status wave_profile_enable(wave_plan_t plan, int enable);
+
+/* Read (and with reset = 1 clear) the counters since the last reset:
+ * pass_launches / pass_ms: pass kernels timed by the events above and their
+ * summed duration (synchronises the plan's stream); point_steps: point
+ * updates those passes performed (grid points x steps); launches: every
+ * kernel of this library launched on the plan.  Any output may be NULL. */
+wave_status wave_profile_read(wave_plan_t plan, int reset, long long* pass_launches, double* pass_ms,
+                              double* point_steps, long long* launches);
+
+/* Destroy the plan and free its device memory.  NULL is accepted. */
+wave_status wave_plan_destroy(wave_plan_t plan);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* wave_last_error(void);
+
+/* ---- tile-legality scheduler (host only, no GPU) --------------------------
+ * Chapter "Time-Tiling" / Section "Skewing Dependencies": a stencil update
+ * reading u[t] at offsets +-r along an axis has the dependence distances
+ * (1, +-r) on that axis; tiling through time is legal once every skewed
+ * distance is lexicographically non-negative, i.e. with skew factor r per
+ * skewed axis.  These calls expose the scheduler for tests and tools. */
+
+/* Skew factor of space order so (= so/2). */
+int wave_skew_factor(int so);
+
+/* Check a tiling for a grid and SO: returns WAVE_OK if the overlapped,
+ * skewed pass schedule is legal and fits the kernel's limits, else
+ * WAVE_ERR_ARG with the reason in wave_last_error(). */
+wave_status wave_tiling_check(const int grid[3], int so, const wave_tiling* tiling);
+
+/* Brute-force legality of the GPU pass schedule on a tiny grid: enumerates
+ * every (point, time level) every thread block computes and checks that each
+ * value it reads is either a pass input or a value the same block computed
+ * earlier from valid inputs, and that every output point is written exactly
+ * once with a valid value.  Returns WAVE_OK or WAVE_ERR_ARG with the first
+ * violation in wave_last_error(). */
+wave_status wave_schedule_verify(const int grid[3], int so, const wave_tiling* tiling);
+
+/* wave_schedule_verify with the kernel's two skew parameters overridden:
+ * `lag` planes between consecutive steps along x (the kernel uses r) and
+ * `halo_per_step` overlapped points per remaining step in y and z (the kernel
+ * uses r).  Smaller values must be rejected; exposed for tests. */
+wave_status wave_schedule_verify_custom(const int grid[3], int so, const wave_tiling* tiling, int lag,
+                                        int halo_per_step);
+
+/* Brute-force check of the paper's skewed time-tiled loop order in 1D+t
+ * (Fig. tiled_skew_snippet / Fig. tiled_256 reduced to one space axis):
+ * tiles of tt time steps x ts skewed points, skew factor `skew`, stencil
+ * radius r, n points, nt steps.  Returns 1 if every point-step runs after
+ * all the point-steps it reads, 0 if a dependence is violated. */
+int wave_skewed_order_legal(int n, int nt, int r, int skew, int tt, int ts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WAVE_H */

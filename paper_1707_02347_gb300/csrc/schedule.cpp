@@ -1,0 +1,298 @@
+// schedule.cpp -- tile-legality scheduler of libwave.so.
+//
+// McCormick 2017, Section "Skewing Dependencies": the acoustic stencil reads
+// u[time] at offsets +-r (r = SO/2) along every axis, i.e. the dependence
+// distance vectors (1, 0, 0, +-r), (1, 0, +-r, 0), (1, +-r, 0, 0).  A tiling
+// through time is legal when every dependence distance, after skewing each
+// tiled space loop by r per time step, is lexicographically non-negative
+// (Section "Legality of Tiling").
+//
+// The GPU schedule (wave_pass.cuh) applies this once per pass of T steps:
+//   * along x, the streamed axis, step k of the pass works r planes behind
+//     step k-1 (skew factor r), so every value a step reads along x has
+//     already been produced by the previous step of the same thread block;
+//   * across y and z each thread block recomputes an overlapped halo of
+//     r (T - k) points at step k, so blocks never wait for each other
+//     inside a pass (the overlap replaces the paper's skewed tile shapes
+//     in the two tiled dimensions, and needs no inter-block ordering);
+//   * reads come only from the pass's input buffer set and writes go to the
+//     other set, so no write-after-read hazard crosses blocks (the paper's
+//     rolling "time dimension buffering" bounds the time tile by the buffer
+//     modulus instead).
+// make_geom() checks the kernel's limits for a tiling; verify_schedule()
+// enumerates the schedule on a small grid and checks every dependence.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "wave_host.h"
+#include "wave_kernels.cuh"
+
+namespace wave {
+
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+int padded_nz(int nz) { return round_up(nz, 4); }
+
+bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std::string* why)
+{
+    auto no = [&](const std::string& s) {
+        if (why) *why = s;
+        return false;
+    };
+    if (R != 2 && R != 4 && R != 8) return no("space order must be 4, 8 or 16");
+    const int maxT = pass_max_threads(R, t.T);
+    if (t.T < 1 || maxT <= 0) return no("no kernel for T = " + std::to_string(t.T) + " at SO " + std::to_string(2 * R));
+    if (t.by < 1) return no("tile by must be >= 1");
+    if (t.bz < 4 || t.bz % 4) return no("tile bz must be a positive multiple of 4");
+    if (t.xc < 1) return no("slab xc must be >= 1");
+    const int nx = grid[0], ny = grid[1], nzp = padded_nz(grid[2]);
+    PassGeom G;
+    G.R = R;
+    G.T = t.T;
+    G.by = t.by;
+    G.bz = t.bz;
+    G.xc = std::min(t.xc, nx);
+    const int halo = R * (t.T - 1);  // overlapped halo of step 1
+    G.zlead = -round_up(halo, 4);
+    G.b_cols = round_up(t.bz + halo, 4) - G.zlead;
+    G.qz = G.b_cols / 4;
+    G.r1y = t.by + 2 * halo;
+    G.b_rows = G.r1y;
+    const int ZH = round_up(R, 4);
+    G.a_rows = G.r1y + 2 * R;
+    G.a_cols = G.b_cols + 2 * ZH;
+    G.threads = G.qz * G.r1y;
+    G.block = round_up(G.threads, 32);
+    if (G.block > maxT)
+        return no("tile needs " + std::to_string(G.block) + " threads, kernel allows " + std::to_string(maxT));
+    if (G.a_cols > 256 || G.a_rows > 256) return no("staged box exceeds the TMA limit of 256 per dimension");
+    G.smem = pass_smem_bytes(R, t.T, G.a_rows, G.a_cols, G.b_rows, G.b_cols, G.block);
+    if (G.smem > 227 * 1024) return no("tile needs " + std::to_string(G.smem) + " bytes of shared memory");
+    G.nty = (ny + t.by - 1) / t.by;
+    G.ntz = (nzp + t.bz - 1) / t.bz;
+    G.nxs = (nx + G.xc - 1) / G.xc;
+    G.blocks = static_cast<long long>(G.nty) * G.ntz * G.nxs;
+    if (G.blocks > 0x7fffffffLL) return no("too many thread blocks");
+    *g = G;
+    return true;
+}
+
+wave_tiling default_tiling(const int grid[3], int R, int T)
+{
+    wave_tiling t{T, 32, 32, 128};
+    if (T == 1) {
+        t.by = 16;
+        t.bz = 64;
+    } else if (R == 2) {
+        t.by = 32;
+        t.bz = 32;
+    } else if (R == 4) {
+        t.by = T == 2 ? 32 : 16;
+        t.bz = T == 2 ? 32 : 24;
+    } else {
+        t.by = 16;
+        t.bz = 32;
+    }
+    t.xc = std::min(grid[0], 128);
+    return t;
+}
+
+std::vector<wave_tiling> tiling_candidates(const int grid[3], int R)
+{
+    std::vector<wave_tiling> out;
+    const int Tmax = R == 2 ? 4 : (R == 4 ? 3 : 2);
+    const int shapes[][2] = {{8, 64}, {16, 32}, {16, 64}, {24, 24}, {24, 32}, {32, 32}, {32, 64}, {40, 40},
+                             {16, 128}, {48, 32}, {32, 48}};
+    const int slabs[] = {64, 128, 256};
+    for (int T = 1; T <= Tmax; ++T)
+        for (auto& s : shapes)
+            for (int xc : slabs) {
+                wave_tiling t{T, s[0], s[1], std::min(xc, grid[0])};
+                PassGeom g;
+                if (make_geom(grid, R, t, &g, nullptr)) {
+                    bool dup = false;
+                    for (auto& o : out) dup = dup || (o.T == t.T && o.by == t.by && o.bz == t.bz && o.xc == t.xc);
+                    if (!dup) out.push_back(t);
+                }
+            }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// Brute-force verification of the pass schedule.
+//
+// Model: one pass of T steps from levels (n-1, n).  For each thread block,
+// step k (1..T) at loop iteration i computes plane x_k = xbase + i - lag k for
+// every column of the block's thread region, when i >= 2 lag k.  A computed
+// value is valid when every value it reads is valid:
+//   u^{n+k-1} at (x_k +- j, y, z), (x_k, y +- j, z), (x_k, y, z +- j), j <= r,
+//   u^{n+k-2} at (x_k, y, z);
+// levels n-1 and n are the pass input (valid everywhere, zero outside the
+// grid); points outside the grid are forced to zero and count as valid.
+// Every output point of levels n+T-1 and n+T must be written exactly once,
+// by its owning block, with a valid value.
+// ---------------------------------------------------------------------------
+static bool verify_schedule(const int grid[3], int R, const wave_tiling& t, int lag, int halo_per_step,
+                            std::string* why)
+{
+    PassGeom g;
+    if (!make_geom(grid, R, t, &g, why)) return false;
+    const int nx = grid[0], ny = grid[1], nz = grid[2];
+    const int T = t.T;
+    // geometry under test: the thread region carries halo_per_step (T-1) rows
+    const int halo = halo_per_step * (T - 1);
+    const int zlead = -round_up(halo, 4);
+    const int b_cols = round_up(t.bz + halo, 4) - zlead;
+    const int r1y = t.by + 2 * halo;
+    auto pidx = [&](int x, int y, int z) { return (static_cast<size_t>(x) * ny + y) * nz + z; };
+    const size_t npts = static_cast<size_t>(nx) * ny * nz;
+    std::vector<int> writes_cur(npts, 0), writes_prev(npts, 0);
+    // valid[k][x][y][z] per block: levels n+k, k = 1..T (index k-1)
+    const int xs_len = g.xc;
+    for (long long b = 0; b < g.blocks; ++b) {
+        long long bb = b;
+        const int tzi = static_cast<int>(bb % g.ntz);
+        bb /= g.ntz;
+        const int tyi = static_cast<int>(bb % g.nty);
+        const int xsi = static_cast<int>(bb / g.nty);
+        const int y0 = tyi * t.by, z0 = tzi * t.bz;
+        const int X0 = xsi * xs_len, X1 = std::min(X0 + xs_len, nx);
+        const int NIT = (X1 - X0) + 2 * lag * T;
+        const int xbase = X0 - lag * T;
+        const int ylo = y0 - halo, zlo = z0 + zlead;
+        // computed[k] over the block's box: x in [xbase - lag T, X1 + lag T), y rows, z cols
+        const int bx0 = xbase - lag * T - 1, bxn = NIT + 2 * lag * T + 2;
+        auto in_region = [&](int y, int z) { return y >= ylo && y < ylo + r1y && z >= zlo && z < zlo + b_cols; };
+        // state: 0 = not computed, 1 = valid, 2 = invalid
+        std::vector<std::vector<char>> st(T + 1,
+                                          std::vector<char>(static_cast<size_t>(bxn) * r1y * b_cols, 0));
+        auto sidx = [&](int x, int y, int z) {
+            return (static_cast<size_t>(x - bx0) * r1y + (y - ylo)) * b_cols + (z - zlo);
+        };
+        auto in_grid = [&](int x, int y, int z) {
+            return x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz;
+        };
+        // value of level n+k (k >= 1) at a point, as seen by this block
+        auto level_valid = [&](int k, int x, int y, int z) -> bool {
+            if (k <= 0) return true;  // pass input (or its zero ghosts)
+            if (!in_grid(x, y, z)) {
+                // ghost: the block forces zero wherever it computes; outside its
+                // region the value is only read if some computed point needs it
+                if (!in_region(y, z) || x - bx0 < 0 || x - bx0 >= bxn) return false;
+                return st[k][sidx(x, y, z)] != 0;
+            }
+            if (!in_region(y, z) || x - bx0 < 0 || x - bx0 >= bxn) return false;
+            return st[k][sidx(x, y, z)] == 1;
+        };
+        for (int i = 0; i < NIT; ++i) {
+            for (int k = 1; k <= T; ++k) {
+                if (i < 2 * lag * k) continue;
+                const int x = xbase + i - lag * k;
+                for (int y = ylo; y < ylo + r1y; ++y)
+                    for (int z = zlo; z < zlo + b_cols; ++z) {
+                        bool ok = true;
+                        if (in_grid(x, y, z)) {
+                            for (int j = -R; j <= R && ok; ++j) {
+                                ok = ok && level_valid(k - 1, x + j, y, z);
+                                ok = ok && level_valid(k - 1, x, y + j, z);
+                                ok = ok && level_valid(k - 1, x, y, z + j);
+                            }
+                            ok = ok && level_valid(k - 2, x, y, z);
+                        }
+                        if (x - bx0 >= 0 && x - bx0 < bxn) st[k][sidx(x, y, z)] = ok ? 1 : 2;
+                    }
+            }
+            // outputs of plane x_T
+            if (i >= 2 * lag * T) {
+                const int x = xbase + i - lag * T;
+                for (int y = y0; y < std::min(y0 + t.by, ny); ++y)
+                    for (int z = z0; z < std::min(z0 + t.bz, nz); ++z) {
+                        if (x < X0 || x >= X1) continue;
+                        if (!level_valid(T, x, y, z) || !level_valid(T - 1, x, y, z)) {
+                            if (why)
+                                *why = "block " + std::to_string(b) + " writes an invalid value at (" +
+                                       std::to_string(x) + "," + std::to_string(y) + "," + std::to_string(z) + ")";
+                            return false;
+                        }
+                        writes_cur[pidx(x, y, z)]++;
+                        writes_prev[pidx(x, y, z)]++;
+                    }
+            }
+        }
+    }
+    for (size_t p = 0; p < npts; ++p)
+        if (writes_cur[p] != 1 || writes_prev[p] != 1) {
+            if (why) *why = "point " + std::to_string(p) + " written " + std::to_string(writes_cur[p]) + " times";
+            return false;
+        }
+    return true;
+}
+
+// Paper's loop order in 1D + t (Fig. tiled_skew_snippet): skewed coordinate
+// x' = x + skew t; tiles of tt steps by ts skewed points, executed in the
+// lexicographic order (time tile, space tile, t, x').  Checks every read of
+// u[t-1][x +- j] (j <= r) and u[t-2][x] happens after its write.
+static bool skewed_order_legal(int n, int nt, int r, int skew, int tt, int ts)
+{
+    if (n <= 2 * r || nt < 1 || tt < 1 || ts < 1 || skew < 0) return false;
+    struct Pt { long long key[4]; int t, x; };
+    std::vector<Pt> pts;
+    for (int t = 1; t <= nt; ++t)
+        for (int x = r; x < n - r; ++x) {
+            const int xs = x + skew * t;
+            pts.push_back({{(t - 1) / tt, xs / ts, t, xs}, t, x});
+        }
+    std::sort(pts.begin(), pts.end(), [](const Pt& a, const Pt& b) {
+        return std::lexicographical_compare(a.key, a.key + 4, b.key, b.key + 4);
+    });
+    std::vector<long long> when(static_cast<size_t>(nt + 1) * n, -1);
+    for (size_t o = 0; o < pts.size(); ++o) when[static_cast<size_t>(pts[o].t) * n + pts[o].x] = static_cast<long long>(o);
+    for (size_t o = 0; o < pts.size(); ++o) {
+        const int t = pts[o].t, x = pts[o].x;
+        for (int j = -r; j <= r; ++j) {
+            const int xx = x + j;
+            if (t - 1 >= 1 && xx >= r && xx < n - r && when[static_cast<size_t>(t - 1) * n + xx] > static_cast<long long>(o))
+                return false;
+        }
+        if (t - 2 >= 1 && when[static_cast<size_t>(t - 2) * n + x] > static_cast<long long>(o)) return false;
+    }
+    return true;
+}
+
+}  // namespace wave
+
+extern "C" int wave_skew_factor(int so) { return so / 2; }
+
+extern "C" wave_status wave_tiling_check(const int grid[3], int so, const wave_tiling* tiling)
+{
+    if (!grid || !tiling) return wave::fail(WAVE_ERR_ARG, "wave_tiling_check: null argument");
+    wave::PassGeom g;
+    std::string why;
+    if (!wave::make_geom(grid, so / 2, *tiling, &g, &why)) return wave::fail(WAVE_ERR_ARG, why);
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_schedule_verify(const int grid[3], int so, const wave_tiling* tiling)
+{
+    if (!grid || !tiling) return wave::fail(WAVE_ERR_ARG, "wave_schedule_verify: null argument");
+    std::string why;
+    if (!wave::verify_schedule(grid, so / 2, *tiling, so / 2, so / 2, &why)) return wave::fail(WAVE_ERR_ARG, why);
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_schedule_verify_custom(const int grid[3], int so, const wave_tiling* tiling, int lag,
+                                                   int halo_per_step)
+{
+    if (!grid || !tiling) return wave::fail(WAVE_ERR_ARG, "wave_schedule_verify_custom: null argument");
+    std::string why;
+    if (!wave::verify_schedule(grid, so / 2, *tiling, lag, halo_per_step, &why))
+        return wave::fail(WAVE_ERR_ARG, why);
+    return WAVE_OK;
+}
+
+extern "C" int wave_skewed_order_legal(int n, int nt, int r, int skew, int tt, int ts)
+{
+    return wave::skewed_order_legal(n, nt, r, skew, tt, ts) ? 1 : 0;
+}

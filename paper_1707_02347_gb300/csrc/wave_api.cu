@@ -1,0 +1,945 @@
+// wave_api.cu -- the C ABI of libwave.so (include/wave.h): plans, passes,
+// forward / adjoint / gradient drivers and the autotuner.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "wave_host.h"
+#include "wave_kernels.cuh"
+
+namespace wave {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+wave_status fail(wave_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+cudaError_t launch_min_positive(const float* m, long long n, int* out, cudaStream_t st);
+
+}  // namespace wave
+
+using namespace wave;
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tap lists of one direction (forward: sources inject, receivers sample;
+// adjoint: the roles swap).
+struct TapSet {
+    int nsrc = 0, nrec = 0, ntaps = 0;
+    int* src_ptr = nullptr;
+    int4* src_ent = nullptr;
+    int* rec_ptr = nullptr;
+    int2* rec_ent = nullptr;
+    int* rec_tptr = nullptr;
+    float* rec_tw = nullptr;
+    void release()
+    {
+        cudaFree(src_ptr); cudaFree(src_ent); cudaFree(rec_ptr); cudaFree(rec_ent); cudaFree(rec_tptr); cudaFree(rec_tw);
+        *this = TapSet();
+    }
+};
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? WAVE_ERR_OOM : WAVE_ERR_CUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+// CK for a launch of one of this library's kernels: also counts it.
+#define CKL(call)           \
+    do {                    \
+        CK(call);           \
+        p->launches++;      \
+    } while (0)
+
+template <class T>
+cudaError_t upload(T** dst, const void* src, size_t bytes, cudaStream_t st)
+{
+    *dst = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);  // the host vectors die after the call
+}
+
+}  // namespace
+
+struct wave_plan_s {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    int n[3] = {0, 0, 0};
+    int nzp = 0;
+    double h[3] = {0, 0, 0};
+    int so = 0, R = 0;
+    double dt = 0.0;
+    int nt = 0;
+    long long npad = 0;
+    wave_options opt{};
+    double vmax_model = 0.0;
+    float* kap = nullptr;
+    float* buf[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* damp = nullptr;  // [nx] [ny] [nzp] profiles
+    int* err = nullptr;
+    int* err_host = nullptr;
+    // sources and receivers
+    std::vector<double> src_xyz, rec_xyz;
+    float* wavelet = nullptr;  // [nt][nsrc]
+    TapSet fwd, adj;
+    bool adj_ready = false;
+    float* slots = nullptr;
+    size_t slots_floats = 0;
+    // coefficients
+    float c0 = 0.f, cx[kMaxR] = {}, cy[kMaxR] = {}, cz[kMaxR] = {};
+    // tiling
+    wave_tiling tiling{};
+    PassGeom geom, geom1;
+    // tensor maps: (pointer, box rows, box cols) -> map
+    std::map<std::tuple<const void*, int, int>, CUtensorMap> maps;
+    // host-buffer entry staging
+    float* stage_m = nullptr;
+    float* stage_w = nullptr;
+    float* stage_r = nullptr;
+    // gradient workspace
+    std::vector<float*> levels;
+    size_t level_count = 0;
+    float* work = nullptr;  // misc device scratch
+    size_t work_bytes = 0;
+    // measurement hook
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double prof_points = 0.0;
+    long long launches = 0;
+};
+
+namespace {
+
+wave_status check_cuda(const char* what, cudaError_t e)
+{
+    if (e == cudaSuccess) return WAVE_OK;
+    return fail(e == cudaErrorMemoryAllocation ? WAVE_ERR_OOM : WAVE_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&old);
+        if (old != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (old >= 0) cudaSetDevice(old);
+    }
+};
+
+// Tensor map of a padded [nx][ny][nzp] float array with a (1, rows, cols) box.
+const CUtensorMap* get_map(wave_plan_t p, const void* ptr, int rows, int cols)
+{
+    auto key = std::make_tuple(ptr, rows, cols);
+    auto it = p->maps.find(key);
+    if (it != p->maps.end()) return &it->second;
+    auto fn = encode_fn();
+    if (!fn) return nullptr;
+    CUtensorMap m;
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(p->nzp), static_cast<cuuint64_t>(p->n[1]),
+                          static_cast<cuuint64_t>(p->n[0])};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(p->nzp) * 4,
+                             static_cast<cuuint64_t>(p->nzp) * 4 * static_cast<cuuint64_t>(p->n[1])};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(cols), static_cast<cuuint32_t>(rows), 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(ptr), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return nullptr;
+    return &(p->maps[key] = m);
+}
+
+PassArgs base_args(wave_plan_t p, const PassGeom& g, const TapSet& taps, const float* wavelet, float* slots)
+{
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = p->n[0];
+    a.ny = p->n[1];
+    a.nz = p->n[2];
+    a.nzp = p->nzp;
+    a.sx = static_cast<long long>(p->n[1]) * p->nzp;
+    a.by = g.by;
+    a.bz = g.bz;
+    a.xc = g.xc;
+    a.nty = g.nty;
+    a.ntz = g.ntz;
+    a.qz = g.qz;
+    a.r1y = g.r1y;
+    a.zlead = g.zlead;
+    a.a_rows = g.a_rows;
+    a.a_cols = g.a_cols;
+    a.b_rows = g.b_rows;
+    a.b_cols = g.b_cols;
+    a.kap = p->kap;
+    a.damp_x = p->damp;
+    a.damp_y = p->damp + p->n[0];
+    a.damp_z = p->damp + p->n[0] + p->n[1];
+    a.inv2dt = static_cast<float>(1.0 / (2.0 * p->dt));
+    a.c0 = p->c0;
+    for (int k = 0; k < kMaxR; ++k) {
+        a.cx[k] = p->cx[k];
+        a.cy[k] = p->cy[k];
+        a.cz[k] = p->cz[k];
+    }
+    a.src_ptr = taps.nsrc ? taps.src_ptr : nullptr;
+    a.src_ent = taps.src_ent;
+    a.wavelet = wavelet;
+    a.nsrc = taps.nsrc;
+    a.rec_ptr = (taps.nrec && slots) ? taps.rec_ptr : nullptr;
+    a.rec_ent = taps.rec_ent;
+    a.slots = slots;
+    a.ntaps = taps.ntaps;
+    a.slot_row0 = 0;
+    a.err = p->err;
+    return a;
+}
+
+// One pass of g.T steps from the state (u^n0, v^{n0-1/2}); writes
+// (u^{n0+T}, v^{n0+T-1/2}) to (out_u, out_v).  out_v may alias v only when
+// g.T == 1 (each point's increment is read and written by the same thread).
+wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const float* wavelet, float* slots, int n0,
+                     const float* u, const float* v, float* out_u, float* out_v)
+{
+    const CUtensorMap* mA = get_map(p, u, g.a_rows, g.a_cols);
+    const CUtensorMap* mV = get_map(p, v, g.b_rows, g.b_cols);
+    const CUtensorMap* mK = get_map(p, p->kap, g.b_rows, g.b_cols);
+    if (!mA || !mV || !mK) return fail(WAVE_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    PassArgs a = base_args(p, g, taps, wavelet, slots);
+    a.n0 = n0;
+    a.out_u = out_u;
+    a.out_v = out_v;
+    cudaError_t e = cudaSuccess;
+    if (p->prof) {
+        if (p->ev_used + 2 > p->ev.size()) {
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t x;
+                CK(cudaEventCreate(&x));
+                p->ev.push_back(x);
+            }
+        }
+        CK(cudaEventRecord(p->ev[p->ev_used], p->st));
+    }
+    if (!launch_pass(p->R, g.T, *mA, *mV, *mK, a, g.block, g.smem, g.blocks, p->st, &e))
+        return fail(WAVE_ERR_ARG, "no kernel for this (SO, T)");
+    p->launches++;
+    if (p->prof) {
+        CK(cudaEventRecord(p->ev[p->ev_used + 1], p->st));
+        p->ev_used += 2;
+        p->prof_points += static_cast<double>(p->n[0]) * p->n[1] * p->n[2] * g.T;
+    }
+    return check_cuda("pass kernel launch", e);
+}
+
+// Field state: (u, v) hold (u^n, v^{n-1/2}); f0, f1 are free buffers.
+struct Fields {
+    float *u, *v, *f0, *f1;
+};
+
+// One pass of g.T steps on the state f.
+wave_status step_pass(wave_plan_t p, const PassGeom& g, Fields* f, const TapSet& taps, const float* wavelet,
+                      float* slots, int n0)
+{
+    if (g.T == 1) {
+        wave_status s = run_pass(p, g, taps, wavelet, slots, n0, f->u, f->v, f->f0, f->v);
+        if (s) return s;
+        std::swap(f->u, f->f0);  // u <- new, f0 <- old u; v updated in place
+        return WAVE_OK;
+    }
+    wave_status s = run_pass(p, g, taps, wavelet, slots, n0, f->u, f->v, f->f0, f->f1);
+    if (s) return s;
+    std::swap(f->u, f->f0);
+    std::swap(f->v, f->f1);
+    return WAVE_OK;
+}
+
+// Advance `steps` steps from level n0 with the plan's tiling (T > 1 passes
+// while they fit, then one-step passes).
+wave_status advance(wave_plan_t p, Fields* f, const TapSet& taps, const float* wavelet, float* slots, int n0,
+                    int steps, bool use_tiling)
+{
+    int n = n0;
+    const int end = n0 + steps;
+    if (use_tiling && p->geom.T > 1) {
+        while (n + p->geom.T <= end) {
+            wave_status s = step_pass(p, p->geom, f, taps, wavelet, slots, n);
+            if (s) return s;
+            n += p->geom.T;
+        }
+    }
+    const PassGeom& g1 = (use_tiling && p->geom.T == 1) ? p->geom : p->geom1;
+    while (n < end) {
+        wave_status s = step_pass(p, g1, f, taps, wavelet, slots, n);
+        if (s) return s;
+        n += 1;
+    }
+    return WAVE_OK;
+}
+
+wave_status finish(wave_plan_t p)
+{
+    cudaError_t e = cudaMemcpyAsync(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) return check_cuda("stream synchronize", e);
+    if (*p->err_host) return fail(WAVE_ERR_TIMEOUT, "a bounded device-side wait gave up (TMA load never completed)");
+    return WAVE_OK;
+}
+
+wave_status build_taps(wave_plan_t p, TapSet* t, int nsrc, const double* sxyz, int nrec, const double* rxyz)
+{
+    t->release();
+    ColumnCsr sc, rc;
+    std::vector<int> tptr;
+    std::vector<float> tw;
+    build_source_csr(nsrc, sxyz, p->h, p->n, p->nzp, &sc);
+    build_receiver_csr(nrec, rxyz, p->h, p->n, p->nzp, &rc, &tptr, &tw);
+    t->nsrc = nsrc;
+    t->nrec = nrec;
+    t->ntaps = static_cast<int>(tw.size());
+    CK(upload(&t->src_ptr, sc.ptr.data(), sc.ptr.size() * 4, p->st));
+    CK(upload(&t->src_ent, sc.ent.data(), sc.ent.size() * 4, p->st));
+    CK(upload(&t->rec_ptr, rc.ptr.data(), rc.ptr.size() * 4, p->st));
+    CK(upload(&t->rec_ent, rc.ent.data(), rc.ent.size() * 4, p->st));
+    CK(upload(&t->rec_tptr, tptr.data(), tptr.size() * 4, p->st));
+    CK(upload(&t->rec_tw, tw.data(), tw.size() * 4, p->st));
+    return WAVE_OK;
+}
+
+wave_status ensure_slots(wave_plan_t p, size_t floats)
+{
+    if (floats <= p->slots_floats) return WAVE_OK;
+    cudaFree(p->slots);
+    p->slots = nullptr;
+    p->slots_floats = 0;
+    CK(cudaMalloc(&p->slots, floats * 4));
+    p->slots_floats = floats;
+    return WAVE_OK;
+}
+
+wave_status ensure_work(wave_plan_t p, size_t bytes)
+{
+    if (bytes <= p->work_bytes) return WAVE_OK;
+    cudaFree(p->work);
+    p->work = nullptr;
+    p->work_bytes = 0;
+    CK(cudaMalloc(&p->work, bytes));
+    p->work_bytes = bytes;
+    return WAVE_OK;
+}
+
+wave_status apply_tiling(wave_plan_t p, const wave_tiling& t)
+{
+    PassGeom g;
+    std::string why;
+    if (!make_geom(p->n, p->R, t, &g, &why)) return fail(WAVE_ERR_ARG, "tiling rejected: " + why);
+    p->tiling = t;
+    p->geom = g;
+    return WAVE_OK;
+}
+
+wave_tiling fill_tiling(wave_plan_t p, wave_tiling t)
+{
+    const int T = t.T > 0 ? t.T : 2;
+    wave_tiling d = default_tiling(p->n, p->R, T);
+    if (t.by <= 0) t.by = d.by;
+    if (t.bz <= 0) t.bz = d.bz;
+    if (t.xc <= 0) t.xc = d.xc;
+    t.T = T;
+    return t;
+}
+
+wave_status set_model_impl(wave_plan_t p, const float* m)
+{
+    const long long n = static_cast<long long>(p->n[0]) * p->n[1] * p->n[2];
+    int* mn = reinterpret_cast<int*>(p->err) + 1;
+    CK(cudaMemsetAsync(mn, 0x7f, sizeof(int), p->st));
+    CKL(launch_min_positive(m, n, mn, p->st));
+    int host_min = 0;
+    CK(cudaMemcpyAsync(&host_min, mn, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    float mmin;
+    std::memcpy(&mmin, &host_min, 4);
+    if (host_min < 0 || !(mmin > 0.f) || !std::isfinite(mmin))
+        return fail(WAVE_ERR_ARG, "model m must be positive and finite everywhere");
+    p->vmax_model = 1.0 / std::sqrt(static_cast<double>(mmin));
+    double dtmax = 0.0;
+    wave_cfl_limit(p->so, p->h, p->vmax_model, &dtmax);
+    if (p->dt > dtmax)
+        return fail(WAVE_ERR_CFL, "dt = " + std::to_string(p->dt) + " ms exceeds the CFL limit " +
+                                      std::to_string(dtmax) + " ms for vmax = " + std::to_string(p->vmax_model));
+    CKL(launch_kappa(m, p->kap, p->n[0], p->n[1], p->n[2], p->nzp, static_cast<float>(p->dt * p->dt), p->st));
+    return WAVE_OK;
+}
+
+wave_status set_damping(wave_plan_t p)
+{
+    const int W = p->opt.sponge_width;
+    const int f = p->opt.sponge_faces;
+    const double vmax = p->opt.vmax > 0.0 ? p->opt.vmax : p->vmax_model;
+    std::vector<float> all, prof;
+    for (int a = 0; a < 3; ++a) {
+        const double dmax = W > 0 ? 3.0 * vmax * std::log(1000.0) / (2.0 * W * p->h[a]) : 0.0;
+        sponge_profile(p->n[a], W, (f >> (2 * a)) & 1, (f >> (2 * a + 1)) & 1, dmax, &prof, a == 2 ? p->nzp : p->n[a]);
+        all.insert(all.end(), prof.begin(), prof.end());
+    }
+    CK(cudaMemcpyAsync(p->damp, all.data(), all.size() * 4, cudaMemcpyHostToDevice, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return WAVE_OK;
+}
+
+void destroy(wave_plan_t p)
+{
+    if (!p) return;
+    DeviceGuard g(p->dev);
+    cudaStreamSynchronize(p->st);
+    cudaFree(p->kap);
+    for (auto& b : p->buf) cudaFree(b);
+    cudaFree(p->damp);
+    cudaFree(p->err);
+    cudaFreeHost(p->err_host);
+    cudaFree(p->wavelet);
+    p->fwd.release();
+    p->adj.release();
+    cudaFree(p->slots);
+    cudaFree(p->stage_m);
+    cudaFree(p->stage_w);
+    cudaFree(p->stage_r);
+    for (auto* l : p->levels) cudaFree(l);
+    cudaFree(p->work);
+    for (auto e : p->ev) cudaEventDestroy(e);
+    delete p;
+}
+
+wave_status forward_impl(wave_plan_t p, const float* u_init, float* rec_out, float* u_final)
+{
+    if (p->fwd.nsrc > 0 && !p->wavelet) return fail(WAVE_ERR_STATE, "sources set without a wavelet");
+    if (p->fwd.nrec > 0 && !rec_out) return fail(WAVE_ERR_ARG, "rec_out is NULL but receivers are set");
+    CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
+    Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
+    if (u_init) {
+        CKL(launch_init_state(u_init, f.u, f.v, p->n[0], p->n[1], p->n[2], p->nzp, p->st));
+    } else {
+        CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
+        CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
+    }
+    float* slots = nullptr;
+    if (p->fwd.nrec > 0 && p->fwd.ntaps > 0) {
+        wave_status s = ensure_slots(p, static_cast<size_t>(p->nt) * p->fwd.ntaps);
+        if (s) return s;
+        slots = p->slots;
+    }
+    wave_status s = advance(p, &f, p->fwd, p->wavelet, slots, 0, p->nt, true);
+    if (s) return s;
+    if (p->fwd.nrec > 0) {
+        if (p->fwd.ntaps > 0)
+            CKL(launch_rec_reduce(slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec_out, p->nt, p->fwd.nrec, p->fwd.ntaps,
+                                 p->st));
+        else
+            CK(cudaMemsetAsync(rec_out, 0, static_cast<size_t>(p->nt) * p->fwd.nrec * 4, p->st));
+    }
+    if (u_final) CKL(launch_final_state(f.u, f.v, u_final, p->n[0], p->n[1], p->n[2], p->nzp, p->st));
+    return WAVE_OK;
+}
+
+wave_status ensure_adjoint_taps(wave_plan_t p)
+{
+    if (p->adj_ready) return WAVE_OK;
+    const int nsrc = static_cast<int>(p->src_xyz.size() / 3), nrec = static_cast<int>(p->rec_xyz.size() / 3);
+    wave_status s = build_taps(p, &p->adj, nrec, p->rec_xyz.data(), nsrc, p->src_xyz.data());
+    if (s) return s;
+    p->adj_ready = true;
+    return WAVE_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" const char* wave_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" wave_status wave_options_default(wave_options* opt)
+{
+    if (!opt) return fail(WAVE_ERR_ARG, "wave_options_default: null");
+    std::memset(opt, 0, sizeof(*opt));
+    opt->sponge_width = 10;
+    opt->sponge_faces = 0x2F;
+    opt->vmax = 0.0;
+    opt->stream = nullptr;
+    opt->autotune = 0;
+    opt->device = -1;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_plan_create(wave_plan_t* out, const int grid[3], const double spacing[3], int so,
+                                        double dt, int nt, const float* m, const wave_options* opt)
+{
+    if (!out || !grid || !spacing || !m) return fail(WAVE_ERR_ARG, "wave_plan_create: null argument");
+    *out = nullptr;
+    if (so != 4 && so != 8 && so != 16) return fail(WAVE_ERR_ARG, "wave_plan_create: so must be 4, 8 or 16");
+    for (int a = 0; a < 3; ++a) {
+        if (grid[a] < so + 1) return fail(WAVE_ERR_ARG, "wave_plan_create: every grid extent must be >= so + 1");
+        if (!(spacing[a] > 0.0) || !std::isfinite(spacing[a]))
+            return fail(WAVE_ERR_ARG, "wave_plan_create: spacing must be positive");
+    }
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(WAVE_ERR_ARG, "wave_plan_create: dt must be positive");
+    if (nt < 0) return fail(WAVE_ERR_ARG, "wave_plan_create: nt must be >= 0");
+    if (static_cast<long long>(grid[1]) * ((grid[2] + 3) / 4) >= (1LL << 31))
+        return fail(WAVE_ERR_ARG, "wave_plan_create: grid too large");
+    wave_options o;
+    wave_options_default(&o);
+    if (opt) o = *opt;
+    if (o.sponge_width < 0) return fail(WAVE_ERR_ARG, "wave_plan_create: sponge_width must be >= 0");
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(WAVE_ERR_CUDA, "no CUDA device");
+    DeviceGuard guard(dev);
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, m) != cudaSuccess || (attr.type != cudaMemoryTypeDevice &&
+                                                               attr.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(WAVE_ERR_ARG, "wave_plan_create: m must be device memory");
+    }
+    auto* p = new wave_plan_s();
+    p->dev = dev;
+    p->st = static_cast<cudaStream_t>(o.stream);
+    p->opt = o;
+    for (int a = 0; a < 3; ++a) {
+        p->n[a] = grid[a];
+        p->h[a] = spacing[a];
+    }
+    p->nzp = padded_nz(grid[2]);
+    p->so = so;
+    p->R = so / 2;
+    p->dt = dt;
+    p->nt = nt;
+    p->npad = static_cast<long long>(grid[0]) * grid[1] * p->nzp;
+    double a[9];
+    fd_weights_exact(so, a);
+    const double ih[3] = {1.0 / (spacing[0] * spacing[0]), 1.0 / (spacing[1] * spacing[1]),
+                          1.0 / (spacing[2] * spacing[2])};
+    p->c0 = static_cast<float>(a[0] * (ih[0] + ih[1] + ih[2]));
+    for (int k = 1; k <= p->R; ++k) {
+        p->cx[k - 1] = static_cast<float>(a[k] * ih[0]);
+        p->cy[k - 1] = static_cast<float>(a[k] * ih[1]);
+        p->cz[k - 1] = static_cast<float>(a[k] * ih[2]);
+    }
+    auto bail = [&](wave_status s) {
+        std::string msg = g_last_error;
+        destroy(p);
+        g_last_error = msg;
+        return s;
+    };
+    cudaError_t e = cudaMalloc(&p->kap, p->npad * 4);
+    for (int b = 0; b < 4 && e == cudaSuccess; ++b) e = cudaMalloc(&p->buf[b], p->npad * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->damp, (grid[0] + grid[1] + p->nzp) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->err, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaHostAlloc(&p->err_host, sizeof(int), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(check_cuda("wave_plan_create allocation", e));
+    }
+    if (cudaMemsetAsync(p->err, 0, 4 * sizeof(int), p->st) != cudaSuccess) return bail(fail(WAVE_ERR_CUDA, "memset"));
+    wave_status s = set_model_impl(p, m);
+    if (s) return bail(s);
+    s = set_damping(p);
+    if (s) return bail(s);
+    // the one-step geometry (remainder steps, adjoint, gradient)
+    std::string why;
+    if (!make_geom(p->n, p->R, default_tiling(p->n, p->R, 1), &p->geom1, &why))
+        return bail(fail(WAVE_ERR_ARG, "no one-step tiling: " + why));
+    wave_tiling t = o.tiling;
+    if (t.T <= 0 && t.by <= 0 && t.bz <= 0 && t.xc <= 0) {
+        t = default_tiling(p->n, p->R, p->R == 8 ? 1 : 2);
+        PassGeom g;
+        if (!make_geom(p->n, p->R, t, &g, nullptr)) t = default_tiling(p->n, p->R, 1);
+    } else {
+        t = fill_tiling(p, t);
+    }
+    s = apply_tiling(p, t);
+    if (s) return bail(s);
+    if (o.autotune) {
+        s = wave_autotune(p, 3, 0, nullptr, nullptr, 0, nullptr);
+        if (s) return bail(s);
+    }
+    *out = p;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_set_model(wave_plan_t p, const float* m)
+{
+    if (!p || !m) return fail(WAVE_ERR_ARG, "wave_set_model: null argument");
+    DeviceGuard g(p->dev);
+    return set_model_impl(p, m);
+}
+
+extern "C" wave_status wave_set_sources(wave_plan_t p, int nsrc, const double* xyz, const float* wavelet)
+{
+    if (!p || nsrc < 0) return fail(WAVE_ERR_ARG, "wave_set_sources: bad argument");
+    if (nsrc > 0 && (!xyz || (!wavelet && p->nt > 0)))
+        return fail(WAVE_ERR_ARG, "wave_set_sources: null positions or wavelet");
+    DeviceGuard g(p->dev);
+    p->src_xyz.assign(xyz, xyz + 3 * static_cast<size_t>(nsrc));
+    p->adj_ready = false;
+    cudaFree(p->wavelet);
+    p->wavelet = nullptr;
+    if (nsrc > 0 && p->nt > 0) {
+        const size_t bytes = static_cast<size_t>(p->nt) * nsrc * 4;
+        CK(cudaMalloc(&p->wavelet, bytes));
+        CK(cudaMemcpyAsync(p->wavelet, wavelet, bytes, cudaMemcpyDefault, p->st));
+    }
+    const int nrec = static_cast<int>(p->rec_xyz.size() / 3);
+    return build_taps(p, &p->fwd, nsrc, p->src_xyz.data(), nrec, p->rec_xyz.data());
+}
+
+extern "C" wave_status wave_set_receivers(wave_plan_t p, int nrec, const double* xyz)
+{
+    if (!p || nrec < 0) return fail(WAVE_ERR_ARG, "wave_set_receivers: bad argument");
+    if (nrec > 0 && !xyz) return fail(WAVE_ERR_ARG, "wave_set_receivers: null positions");
+    DeviceGuard g(p->dev);
+    p->rec_xyz.assign(xyz, xyz + 3 * static_cast<size_t>(nrec));
+    p->adj_ready = false;
+    const int nsrc = static_cast<int>(p->src_xyz.size() / 3);
+    return build_taps(p, &p->fwd, nsrc, p->src_xyz.data(), nrec, p->rec_xyz.data());
+}
+
+extern "C" wave_status wave_set_tiling(wave_plan_t p, const wave_tiling* t)
+{
+    if (!p || !t) return fail(WAVE_ERR_ARG, "wave_set_tiling: null argument");
+    return apply_tiling(p, fill_tiling(p, *t));
+}
+
+extern "C" wave_status wave_get_tiling(wave_plan_t p, wave_tiling* t)
+{
+    if (!p || !t) return fail(WAVE_ERR_ARG, "wave_get_tiling: null argument");
+    *t = p->tiling;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave_tiling* cand, double* ms_per_step,
+                                     int cap, int* ncand)
+{
+    if (!p || passes < 1) return fail(WAVE_ERR_ARG, "wave_autotune: bad argument");
+    DeviceGuard g(p->dev);
+    auto cands = tiling_candidates(p->n, p->R);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
+    CK(cudaMemsetAsync(p->buf[0], 0, p->npad * 4, p->st));
+    CK(cudaMemsetAsync(p->buf[1], 0, p->npad * 4, p->st));
+    double best = 1e300;
+    wave_tiling best_t = p->tiling;
+    int count = 0;
+    TapSet none;
+    for (auto& t : cands) {
+        if (T_only > 0 && t.T != T_only) continue;
+        PassGeom geom;
+        if (!make_geom(p->n, p->R, t, &geom, nullptr)) continue;
+        Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
+        auto one = [&](int n0) -> wave_status { return step_pass(p, geom, &f, none, nullptr, nullptr, n0); };
+        wave_status s = one(0);
+        if (s) return s;
+        CK(cudaEventRecord(e0, p->st));
+        for (int k = 0; k < passes; ++k) {
+            s = one(0);
+            if (s) return s;
+        }
+        CK(cudaEventRecord(e1, p->st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per_step = ms / (passes * geom.T);
+        if (cand && count < cap) cand[count] = t;
+        if (ms_per_step && count < cap) ms_per_step[count] = per_step;
+        ++count;
+        if (per_step < best) {
+            best = per_step;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ncand) *ncand = count;
+    wave_status s = finish(p);
+    if (s) return s;
+    return apply_tiling(p, best_t);
+}
+
+extern "C" wave_status wave_forward(wave_plan_t p, const float* u_init, float* rec_out, float* u_final)
+{
+    if (!p) return fail(WAVE_ERR_ARG, "wave_forward: null plan");
+    DeviceGuard g(p->dev);
+    wave_status s = forward_impl(p, u_init, rec_out, u_final);
+    if (s) return s;
+    return finish(p);
+}
+
+extern "C" wave_status wave_forward_host(wave_plan_t p, const float* m_host, const float* wavelet_host,
+                                         float* rec_host)
+{
+    if (!p || !m_host) return fail(WAVE_ERR_ARG, "wave_forward_host: null argument");
+    DeviceGuard g(p->dev);
+    const size_t nm = static_cast<size_t>(p->n[0]) * p->n[1] * p->n[2];
+    const int nsrc = static_cast<int>(p->src_xyz.size() / 3), nrec = static_cast<int>(p->rec_xyz.size() / 3);
+    if (nsrc > 0 && !wavelet_host) return fail(WAVE_ERR_ARG, "wave_forward_host: null wavelet");
+    if (nrec > 0 && !rec_host) return fail(WAVE_ERR_ARG, "wave_forward_host: null rec");
+    if (!p->stage_m) CK(cudaMalloc(&p->stage_m, nm * 4));
+    if (nrec > 0 && !p->stage_r) CK(cudaMalloc(&p->stage_r, static_cast<size_t>(p->nt) * nrec * 4));
+    CK(cudaMemcpyAsync(p->stage_m, m_host, nm * 4, cudaMemcpyHostToDevice, p->st));
+    wave_status s = set_model_impl(p, p->stage_m);
+    if (s) return s;
+    if (nsrc > 0 && p->nt > 0) {
+        if (!p->wavelet) CK(cudaMalloc(&p->wavelet, static_cast<size_t>(p->nt) * nsrc * 4));
+        CK(cudaMemcpyAsync(p->wavelet, wavelet_host, static_cast<size_t>(p->nt) * nsrc * 4, cudaMemcpyHostToDevice,
+                           p->st));
+    }
+    s = forward_impl(p, nullptr, nrec > 0 ? p->stage_r : nullptr, nullptr);
+    if (s) return s;
+    if (nrec > 0)
+        CK(cudaMemcpyAsync(rec_host, p->stage_r, static_cast<size_t>(p->nt) * nrec * 4, cudaMemcpyDeviceToHost,
+                           p->st));
+    return finish(p);
+}
+
+extern "C" wave_status wave_adjoint(wave_plan_t p, const float* rec_resid, float* src_out)
+{
+    if (!p || !rec_resid || !src_out) return fail(WAVE_ERR_ARG, "wave_adjoint: null argument");
+    DeviceGuard g(p->dev);
+    wave_status s = ensure_adjoint_taps(p);
+    if (s) return s;
+    const int nsrc = p->adj.nrec, nrec = p->adj.nsrc;  // forward roles
+    if (nsrc == 0 || nrec == 0) return fail(WAVE_ERR_STATE, "wave_adjoint: needs sources and receivers");
+    const size_t wbytes = static_cast<size_t>(p->nt) * nrec * 4, obytes = static_cast<size_t>(p->nt) * nsrc * 4;
+    s = ensure_work(p, wbytes + 2 * obytes + 256);
+    if (s) return s;
+    float* wrev = p->work;
+    float* orev = reinterpret_cast<float*>(reinterpret_cast<char*>(p->work) + ((wbytes + 255) & ~size_t(255)));
+    CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
+    CKL(launch_reverse_rows(rec_resid, wrev, p->nt, nrec, p->st));
+    Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
+    CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
+    CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
+    float* slots = nullptr;
+    if (p->adj.ntaps > 0) {
+        s = ensure_slots(p, static_cast<size_t>(p->nt) * p->adj.ntaps);
+        if (s) return s;
+        slots = p->slots;
+    }
+    s = advance(p, &f, p->adj, wrev, slots, 0, p->nt, true);
+    if (s) return s;
+    if (p->adj.ntaps > 0)
+        CKL(launch_rec_reduce(slots, p->adj.rec_tptr, p->adj.rec_tw, orev, p->nt, nsrc, p->adj.ntaps, p->st));
+    else
+        CK(cudaMemsetAsync(orev, 0, obytes, p->st));
+    CKL(launch_reverse_rows(orev, src_out, p->nt, nsrc, p->st));
+    return finish(p);
+}
+
+extern "C" wave_status wave_gradient(wave_plan_t p, const float* d_obs, float* grad_m, double* misfit,
+                                     int checkpoint_every)
+{
+    if (!p || !d_obs || !grad_m) return fail(WAVE_ERR_ARG, "wave_gradient: null argument");
+    if (checkpoint_every < 0) return fail(WAVE_ERR_ARG, "wave_gradient: checkpoint_every must be >= 0");
+    DeviceGuard g(p->dev);
+    const int nt = p->nt;
+    const int nsrc = p->fwd.nsrc, nrec = p->fwd.nrec;
+    if (nsrc == 0 || nrec == 0 || !p->wavelet) return fail(WAVE_ERR_STATE, "wave_gradient: needs sources and receivers");
+    wave_status s = ensure_adjoint_taps(p);
+    if (s) return s;
+    // K: segment length; the increments of a whole segment are kept during its adjoint sweep
+    int K = checkpoint_every;
+    if (K == 0 || K > nt) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        const size_t need = static_cast<size_t>(nt + 3) * p->npad * 4;
+        K = need + (size_t(4) << 30) < fr ? std::max(nt, 1) : std::max(1, static_cast<int>(std::sqrt(double(nt))));
+    }
+    const int nseg = nt > 0 ? (nt + K - 1) / K : 0;
+    const size_t nlev = static_cast<size_t>(2 * nseg) + (K + 1) + 1;
+    while (p->levels.size() < nlev) {
+        float* l = nullptr;
+        CK(cudaMalloc(&l, p->npad * 4));
+        p->levels.push_back(l);
+    }
+    float** ck = p->levels.data();                  // [2 nseg]: (u^{cK}, v^{cK-1/2})
+    float** seg = p->levels.data() + 2 * nseg;      // [K + 1]: v^{t0-1/2} .. v^{t0+K-1/2}
+    float* uspare = p->levels[2 * nseg + K + 1];    // second u buffer of the recompute
+    const size_t rbytes = static_cast<size_t>(nt) * nrec * 4;
+    s = ensure_work(p, 2 * rbytes + 256 * 8 + 1024);
+    if (s) return s;
+    float* rec = p->work;
+    float* rrev = reinterpret_cast<float*>(reinterpret_cast<char*>(p->work) + ((rbytes + 255) & ~size_t(255)));
+    double* partial = reinterpret_cast<double*>(reinterpret_cast<char*>(rrev) + ((rbytes + 255) & ~size_t(255)));
+    CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
+    // 1) forward, keeping a checkpoint at the start of every segment
+    s = ensure_slots(p, static_cast<size_t>(nt) * std::max(p->fwd.ntaps, p->adj.ntaps));
+    if (s) return s;
+    Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
+    CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
+    CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
+    for (int c = 0; c < nseg; ++c) {
+        CK(cudaMemcpyAsync(ck[2 * c], f.u, p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
+        CK(cudaMemcpyAsync(ck[2 * c + 1], f.v, p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
+        const int steps = std::min(K, nt - c * K);
+        s = advance(p, &f, p->fwd, p->wavelet, p->slots, c * K, steps, true);
+        if (s) return s;
+    }
+    if (p->fwd.ntaps > 0)
+        CKL(launch_rec_reduce(p->slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec, nt, nrec, p->fwd.ntaps, p->st));
+    else
+        CK(cudaMemsetAsync(rec, 0, rbytes, p->st));
+    // 2) residual (time-reversed) and misfit
+    CKL(launch_residual(rec, d_obs, rrev, partial, nt, nrec, p->st));
+    std::vector<double> hp(256);
+    CK(cudaMemcpyAsync(hp.data(), partial, 256 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    // 3) adjoint sweep, segment by segment (the adjoint runs the same update backwards)
+    Fields a{p->buf[2], p->buf[3], p->buf[1], nullptr};  // (mu, its increment), spare
+    CK(cudaMemsetAsync(a.u, 0, p->npad * 4, p->st));
+    CK(cudaMemsetAsync(a.v, 0, p->npad * 4, p->st));
+    float* gacc = p->buf[0];  // gradient accumulator (padded layout)
+    CK(cudaMemsetAsync(gacc, 0, p->npad * 4, p->st));
+    const float scale = static_cast<float>(1.0 / (p->dt * p->dt));
+    for (int c = nseg - 1; c >= 0; --c) {
+        const int t0 = c * K;
+        const int steps = std::min(K, nt - t0);
+        // recompute the increments v^{t0+1/2} .. v^{t0+steps-1/2} into seg[1 ..]
+        float* uu[2] = {ck[2 * c], uspare};
+        CK(cudaMemcpyAsync(seg[0], ck[2 * c + 1], p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
+        for (int l = 0; l < steps; ++l) {
+            s = run_pass(p, p->geom1, p->fwd, p->wavelet, nullptr, t0 + l, uu[l & 1], seg[l], uu[(l + 1) & 1],
+                         seg[l + 1]);
+            if (s) return s;
+        }
+        // (the checkpoint's u buffer is reused by the recompute: each segment is visited once)
+        // adjoint steps j = t0+steps .. t0+1: mu^j from the adjoint state, source r^{j-1}
+        for (int j = t0 + steps; j >= t0 + 1; --j) {
+            const int sidx = nt - j;  // forward-order index of this adjoint step
+            s = step_pass(p, p->geom1, &a, p->adj, rrev, nullptr, sidx);
+            if (s) return s;
+            // D_tt u^{j-1} = (v^{j-1/2} - v^{j-3/2}) / dt^2 ; seg[l] = v^{t0+l-1/2}
+            const int l = j - t0;
+            CKL(launch_grad_accum(gacc, a.u, seg[l], seg[l - 1], p->npad, scale, p->st));
+        }
+    }
+    CKL(launch_unpad_grad(gacc, grad_m, p->n[0], p->n[1], p->n[2], p->nzp, p->st));
+    s = finish(p);
+    if (s) return s;
+    if (misfit) {
+        double J = 0.0;
+        for (double v : hp) J += v;
+        *misfit = 0.5 * J;
+    }
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_profile_enable(wave_plan_t p, int enable)
+{
+    if (!p) return fail(WAVE_ERR_ARG, "wave_profile_enable: null plan");
+    p->prof = enable != 0;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_profile_read(wave_plan_t p, int reset, long long* pass_launches, double* pass_ms,
+                                         double* point_steps, long long* launches)
+{
+    if (!p) return fail(WAVE_ERR_ARG, "wave_profile_read: null plan");
+    DeviceGuard g(p->dev);
+    CK(cudaStreamSynchronize(p->st));
+    double ms = 0.0;
+    for (size_t k = 0; k + 1 < p->ev_used; k += 2) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, p->ev[k], p->ev[k + 1]));
+        ms += t;
+    }
+    if (pass_launches) *pass_launches = static_cast<long long>(p->ev_used / 2);
+    if (pass_ms) *pass_ms = ms;
+    if (point_steps) *point_steps = p->prof_points;
+    if (launches) *launches = p->launches;
+    if (reset) {
+        p->ev_used = 0;
+        p->prof_points = 0.0;
+        p->launches = 0;
+    }
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_plan_destroy(wave_plan_t p)
+{
+    destroy(p);
+    return WAVE_OK;
+}
+
+namespace wave {
+
+namespace {
+__global__ void min_positive_kernel(const float* __restrict__ m, long long n, int* out)
+{
+    int best = 0x7f7fffff;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float v = m[i];
+        int b = __float_as_int(v);
+        if (!(v > 0.f) || !isfinite(v)) b = -1;  // invalid marks as negative
+        best = (b < 0 || best < 0) ? -1 : min(best, b);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const int other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = (other < 0 || best < 0) ? -1 : min(best, other);
+    }
+    if ((threadIdx.x & 31) == 0) atomicMin(out, best);
+}
+}  // namespace
+
+cudaError_t launch_min_positive(const float* m, long long n, int* out, cudaStream_t st)
+{
+    long long b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    min_positive_kernel<<<static_cast<unsigned>(b), 256, 0, st>>>(m, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace wave

@@ -1,0 +1,79 @@
+// wave_kernels.cuh -- device-side interface shared by the kernels and the
+// host code of libwave.so.  Nothing here is visible through the C ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wave {
+
+constexpr int kMaxR = 8;
+
+// Geometry and inputs of one pass of the pipelined kernel (see wave_kernels.cu).
+struct PassArgs {
+    int nx, ny, nz, nzp;    // grid; nzp = z extent of the padded device layout
+    long long sx;           // elements per x plane of the padded layout (ny * nzp)
+    int by, bz, xc;         // output tile along y, z and x-slab length
+    int nty, ntz;           // tiles along y and z
+    int qz, r1y;            // threads per row (z quads) and rows of the thread region
+    int zlead;              // z of the thread region relative to the tile's z0 (<= 0, multiple of 4)
+    int a_rows, a_cols;     // staged box of u^n (thread region plus the stencil halo)
+    int b_rows, b_cols;     // staged box of v^{n-1/2} and kappa (the thread region)
+    float* out_u;           // receives u^{n+T}
+    float* out_v;           // receives v^{n+T-1/2} = u^{n+T} - u^{n+T-1} (may alias the input for T = 1)
+    const float* kap;       // kappa = dt^2 / m, padded layout
+    const float* damp_x;    // sponge profile per axis: d(x,y,z) = dx[x] + (dy[y] + dz[z])
+    const float* damp_y;
+    const float* damp_z;
+    float inv2dt;           // 1 / (2 dt)
+    float c0;               // a_0 (1/hx^2 + 1/hy^2 + 1/hz^2)
+    float cx[kMaxR], cy[kMaxR], cz[kMaxR];  // a_k / h^2 per axis
+    int n0;                 // time level n at the start of the pass
+    // sources: per z-quad column CSR of {x, lane, source, weight bits}, sorted by x
+    const int* src_ptr;
+    const int4* src_ent;
+    const float* wavelet;   // [nt][nsrc]
+    int nsrc;
+    // receivers: per column CSR of {x, (tap << 2) | lane}; values go to slots
+    const int* rec_ptr;
+    const int2* rec_ent;
+    float* slots;           // [rows][ntaps]
+    int ntaps;
+    int slot_row0;          // rec row stored in slot row 0
+    int* err;               // device error word (bit 0: a bounded wait gave up)
+};
+
+// Launch one pass with R = so/2 and T steps from the state (u^n, v^{n-1/2})
+// (mapA over u^n, mapV over v^{n-1/2}, mapK over kappa).  Returns false if the
+// (R, T) pair has no instantiation.
+bool launch_pass(int R, int T, const CUtensorMap& mapA, const CUtensorMap& mapP, const CUtensorMap& mapK,
+                 const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st,
+                 cudaError_t* err);
+
+// Largest thread block the (R, T) instantiation was compiled for.
+int pass_max_threads(int R, int T);
+
+// Shared memory bytes of a pass with this geometry.
+size_t pass_smem_bytes(int R, int T, int a_rows, int a_cols, int b_rows, int b_cols, int block);
+
+// Elementwise helpers.
+cudaError_t launch_kappa(const float* m, float* kap, int nx, int ny, int nz, int nzp, float dt2, cudaStream_t st);
+cudaError_t launch_pad_copy(const float* src, float* dst, int nx, int ny, int nz, int nzp, cudaStream_t st);
+cudaError_t launch_unpad_copy(const float* src, float* dst, int nx, int ny, int nz, int nzp, cudaStream_t st);
+// (u^{-1}, u^0) dense -> state u = u^0, v = u^0 - u^{-1} (padded)
+cudaError_t launch_init_state(const float* u2, float* u, float* v, int nx, int ny, int nz, int nzp, cudaStream_t st);
+// state (u, v) padded -> dense (u - v, u)
+cudaError_t launch_final_state(const float* u, const float* v, float* u2, int nx, int ny, int nz, int nzp,
+                               cudaStream_t st);
+cudaError_t launch_rec_reduce(const float* slots, const int* tptr, const float* tw, float* rec, int rows,
+                              int nrec, int ntaps, cudaStream_t st);
+// grad -= scale * mu * (v_new - v_old)   (scale = 1/dt^2)
+cudaError_t launch_grad_accum(float* grad, const float* mu, const float* v_new, const float* v_old, long long n,
+                              float scale, cudaStream_t st);
+cudaError_t launch_unpad_grad(const float* src, float* dst, int nx, int ny, int nz, int nzp, cudaStream_t st);
+cudaError_t launch_residual(const float* rec, const float* dobs, float* resid_rev, double* partial, int nt,
+                            int nrec, cudaStream_t st);
+cudaError_t launch_reverse_rows(const float* src, float* dst, int nt, int ncol, cudaStream_t st);
+
+}  // namespace wave

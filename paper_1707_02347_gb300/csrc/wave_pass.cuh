@@ -1,0 +1,490 @@
+// wave_pass.cuh -- the pipelined pass kernel of libwave.so (instantiated per
+// stencil radius in wave_pass_r*.cu).
+//
+// The kernel advances the damped acoustic wave equation
+//     u^{n+1} = ((dt d - 2m) u^{n-1} + 4m u^n + 2dt^2 (L_h u^n + q^n)) / (dt d + 2m)
+// (McCormick 2017, Fig. acoustic_devito).  Dividing by 2m and writing the
+// increment v^{n+1/2} = u^{n+1} - u^n gives the same recurrence as
+//     v^{n+1/2} = ((1 - g) v^{n-1/2} + kappa (L_h u^n + q^n)) / (1 + g),
+//     u^{n+1}   = u^n + v^{n+1/2},
+//     kappa = dt^2 / m,  g = dt d / (2m) = d kappa / (2 dt),
+// which the kernel steps with the state (u^n, v^{n-1/2}).  In exact
+// arithmetic the two are identical; in float32 carrying v keeps the rounding
+// of u^{n+1} out of the velocity, where leapfrog would amplify it by
+// 1 / sin(omega dt) at every step.
+//
+// One pass advances T time steps over HBM (Chapter "Time-Tiling").  Each
+// thread block owns an output tile by x bz in the y-z plane and streams
+// through a slab of x planes.  The T steps form a pipeline along x: step k
+// works on plane x_k = x_0 - k r (r = SO/2), r planes behind step k-1 -- the
+// skew by r per time step that makes tiling through time legal (Section
+// "Skewing Dependencies").  In the y-z plane the tile carries an overlapped
+// halo of r (T - k) points at step k, so no block depends on another within a
+// pass; outputs go to a second buffer set, so no write-after-read hazard
+// crosses blocks (the paper's rolling time buffer bounds the time tile by its
+// modulus instead, Section "Time Dimension Buffering").
+//
+// Data movement per iteration (one x plane per step):
+//   * TMA (cp.async.bulk.tensor) stages the plane of u^n with its halo, and
+//     the planes of v^{n-1/2} and kappa, into a shared-memory ring completed
+//     on mbarriers; out-of-range boxes are zero-filled by the TMA unit, which
+//     is the zero Dirichlet ghost layer.
+//   * Every thread owns a column of 4 consecutive z points (128-bit loads and
+//     stores) and keeps, per step, a register queue of the 2r + 1 planes of
+//     its column along x: the x neighbours never touch shared memory.
+//   * In-plane (y, z) neighbours of step k come from shared memory: step 1
+//     reads the TMA ring, step k >= 2 a plane buffer that the threads fill
+//     from the centres of their queues once per iteration.
+//   * The increment of step k-1 at plane x_k, produced r iterations earlier,
+//     waits in a thread-private shared-memory ring until step k needs it.
+//   * One __syncthreads per iteration.
+//
+// Every arithmetic operation of the point update is an explicit
+// round-to-nearest intrinsic in one fixed order (centre, y pairs, z pairs,
+// x pairs, sources, increment, field), so a pass with T = 1 and passes with
+// T > 1 produce bit-identical fields: tiling only reorders independent
+// updates.
+#pragma once
+#include "wave_kernels.cuh"
+
+#include <climits>
+#include <type_traits>
+#include <utility>
+
+namespace wave {
+namespace detail {
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bound on any wait: 2 s
+
+template <int R, int T>
+struct Cfg {
+    static constexpr int D = (R == 8) ? 2 : 3;    // iterations loaded ahead
+    static constexpr int P = 2 * R + 1;           // queue length along x
+    static constexpr int ZH = (R + 3) & ~3;       // z halo of the staged box, rounded to 4
+    static constexpr int NQ = ZH / 4;             // halo quads on each side
+    static constexpr int NA = D + R + 1;          // ring slots of u^n planes
+    static constexpr int NB = D + 1;              // ring slots of (v^{n-1/2}, kappa) planes
+    static constexpr int NV = R + 1;              // delay slots of the increments (steps >= 2)
+    static constexpr int MAXT = (T * P * 4 > 100) ? 384 : 512;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+template <int... Is, class F>
+__device__ __forceinline__ void static_for_impl(std::integer_sequence<int, Is...>, F& f)
+{
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+
+// f(std::integral_constant<int, S>) for S = 0 .. N-1, fully unrolled.
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    static_for_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float lane_of(const float4& v, int l)
+{
+    return l == 0 ? v.x : (l == 1 ? v.y : (l == 2 ? v.z : v.w));
+}
+
+// L_h u at the 4 points of a column quad, in the one fixed order every kernel
+// uses: centre, then y pairs k = 1..r, then z pairs, then x pairs.
+// plane: shared-memory plane holding u of this step's input level at the
+// current x with a halo of r rows and ZH columns; pos: the quad's own index;
+// q: the x queue, logical index j at physical (S + j) % P.
+template <int R, int S>
+__device__ __forceinline__ float4 laplacian4(const float* plane, int pos, int pitch, const float4 (&q)[2 * R + 1],
+                                             const PassArgs& a)
+{
+    constexpr int P = 2 * R + 1;
+    constexpr int NQ = ((R + 3) & ~3) / 4;
+    const float4 c = q[(S + R) % P];
+    float L[4] = {__fmul_rn(a.c0, c.x), __fmul_rn(a.c0, c.y), __fmul_rn(a.c0, c.z), __fmul_rn(a.c0, c.w)};
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+        const float4 m = lds4(plane + pos - k * pitch);
+        const float4 p = lds4(plane + pos + k * pitch);
+        L[0] = __fmaf_rn(a.cy[k - 1], __fadd_rn(m.x, p.x), L[0]);
+        L[1] = __fmaf_rn(a.cy[k - 1], __fadd_rn(m.y, p.y), L[1]);
+        L[2] = __fmaf_rn(a.cy[k - 1], __fadd_rn(m.z, p.z), L[2]);
+        L[3] = __fmaf_rn(a.cy[k - 1], __fadd_rn(m.w, p.w), L[3]);
+    }
+    float v[4 * (2 * NQ + 1)];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        const float4 lft = lds4(plane + pos - 4 * (NQ - j));
+        const float4 rgt = lds4(plane + pos + 4 * (j + 1));
+        v[4 * j + 0] = lft.x; v[4 * j + 1] = lft.y; v[4 * j + 2] = lft.z; v[4 * j + 3] = lft.w;
+        v[4 * (NQ + 1 + j) + 0] = rgt.x; v[4 * (NQ + 1 + j) + 1] = rgt.y;
+        v[4 * (NQ + 1 + j) + 2] = rgt.z; v[4 * (NQ + 1 + j) + 3] = rgt.w;
+    }
+    v[4 * NQ + 0] = c.x; v[4 * NQ + 1] = c.y; v[4 * NQ + 2] = c.z; v[4 * NQ + 3] = c.w;
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+            L[l] = __fmaf_rn(a.cz[k - 1], __fadd_rn(v[4 * NQ + l - k], v[4 * NQ + l + k]), L[l]);
+    }
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+        const float4 m = q[(S + R - k) % P];
+        const float4 p = q[(S + R + k) % P];
+        L[0] = __fmaf_rn(a.cx[k - 1], __fadd_rn(m.x, p.x), L[0]);
+        L[1] = __fmaf_rn(a.cx[k - 1], __fadd_rn(m.y, p.y), L[1]);
+        L[2] = __fmaf_rn(a.cx[k - 1], __fadd_rn(m.z, p.z), L[2]);
+        L[3] = __fmaf_rn(a.cx[k - 1], __fadd_rn(m.w, p.w), L[3]);
+    }
+    return make_float4(L[0], L[1], L[2], L[3]);
+}
+
+// New increment of one point: ((1 - g) v + kappa L) / (1 + g), g = d kappa / (2 dt).
+// With g == 0 both branches give the same bits ((1 - 0) v is v, x / 1 is x),
+// so the branch taken never changes a result.
+__device__ __forceinline__ float increment(float L, float v, float kap, float g)
+{
+    if (g == 0.f) return __fmaf_rn(kap, L, v);
+    return __fdiv_rn(__fmaf_rn(kap, L, __fmaf_rn(-g, v, v)), __fadd_rn(1.f, g));
+}
+
+__device__ __forceinline__ void update4(const float4& L, float4& u, float4& v, const float4& kap, float dx,
+                                        const float (&dyz)[4], bool dyz_zero, float inv2dt)
+{
+    if (dx == 0.f && dyz_zero) {
+        v.x = __fmaf_rn(kap.x, L.x, v.x);
+        v.y = __fmaf_rn(kap.y, L.y, v.y);
+        v.z = __fmaf_rn(kap.z, L.z, v.z);
+        v.w = __fmaf_rn(kap.w, L.w, v.w);
+    } else {
+        v.x = increment(L.x, v.x, kap.x, __fmul_rn(__fmul_rn(__fadd_rn(dx, dyz[0]), kap.x), inv2dt));
+        v.y = increment(L.y, v.y, kap.y, __fmul_rn(__fmul_rn(__fadd_rn(dx, dyz[1]), kap.y), inv2dt));
+        v.z = increment(L.z, v.z, kap.z, __fmul_rn(__fmul_rn(__fadd_rn(dx, dyz[2]), kap.z), inv2dt));
+        v.w = increment(L.w, v.w, kap.w, __fmul_rn(__fmul_rn(__fadd_rn(dx, dyz[3]), kap.w), inv2dt));
+    }
+    u.x = __fadd_rn(u.x, v.x);
+    u.y = __fadd_rn(u.y, v.y);
+    u.z = __fadd_rn(u.z, v.z);
+    u.w = __fadd_rn(u.w, v.w);
+}
+
+// First CSR entry of [lo, hi) whose x is >= x0.
+template <class E>
+__device__ __forceinline__ int first_at_or_after(const E* ent, int lo, int hi, int x0)
+{
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ent[mid].x < x0) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+template <int R, int T>
+__global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
+    pass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
+                const __grid_constant__ CUtensorMap mapK, const PassArgs a)
+{
+    using C = Cfg<R, T>;
+    constexpr int P = C::P, NA = C::NA, NB = C::NB, NV = C::NV, ZH = C::ZH, kPrefetch = C::D;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(smem + 8 * (NA + NB));
+    const uint32_t abytes = (static_cast<uint32_t>(a.a_rows * a.a_cols * 4) + 127u) & ~127u;
+    const uint32_t bbytes = (static_cast<uint32_t>(a.b_rows * a.b_cols * 4) + 127u) & ~127u;
+    const uint32_t hdr = (8u * (NA + NB) + 4u + 127u) & ~127u;
+    float* ringA = reinterpret_cast<float*>(smem + hdr);
+    float* ringB = reinterpret_cast<float*>(smem + hdr + NA * abytes);
+    float* planes = reinterpret_cast<float*>(smem + hdr + NA * abytes + NB * 2 * bbytes);
+    float4* vring = reinterpret_cast<float4*>(smem + hdr + NA * abytes + NB * 2 * bbytes + 2 * (T - 1) * abytes);
+    const uint32_t txA = static_cast<uint32_t>(a.a_rows * a.a_cols * 4);
+    const uint32_t txB = static_cast<uint32_t>(2 * a.b_rows * a.b_cols * 4);
+    const int afl = static_cast<int>(abytes / 4), bfl = static_cast<int>(bbytes / 4);
+
+    // thread block -> tile (z fastest, then y, then x slab)
+    long long blk = blockIdx.x;
+    const int tzi = static_cast<int>(blk % a.ntz);
+    blk /= a.ntz;
+    const int tyi = static_cast<int>(blk % a.nty);
+    const int xsi = static_cast<int>(blk / a.nty);
+    const int y0 = tyi * a.by, z0 = tzi * a.bz;
+    const int X0 = xsi * a.xc, X1 = min(X0 + a.xc, a.nx);
+    const int NIT = (X1 - X0) + 2 * R * T;
+    const int xbase = X0 - R * T;  // x_0 of iteration 0
+    const int ylo = y0 - R * (T - 1), zlo = z0 + a.zlead;
+
+    // thread -> column quad
+    const int tid = threadIdx.x;
+    const int nthr = a.qz * a.r1y;
+    const bool act = tid < nthr;
+    const int ty = act ? tid / a.qz : 0, tq = act ? tid % a.qz : 0;
+    const int gy = ylo + ty, gz = zlo + 4 * tq;
+    const bool colv = act && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nzp;
+    const bool partial = colv && (gz + 4 > a.nz);
+    const bool own = colv && gy >= y0 && gy < y0 + a.by && gz >= z0 && gz < z0 + a.bz;
+    const int pitch = a.a_cols;
+    const int posA = (ty + R) * pitch + ZH + 4 * tq;
+    const int posB = ty * a.b_cols + 4 * tq;
+    const long long colofs = static_cast<long long>(colv ? gy : 0) * a.nzp + (colv ? gz : 0);
+    const int col = colv ? gy * (a.nzp >> 2) + (gz >> 2) : 0;
+
+    float dyz[4] = {0.f, 0.f, 0.f, 0.f};
+    bool dyz_zero = true;
+    if (colv) {
+        const float dyv = a.damp_y[gy];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            dyz[l] = __fadd_rn(dyv, a.damp_z[gz + l]);
+            dyz_zero = dyz_zero && (dyz[l] == 0.f);
+        }
+    }
+
+    // source and receiver cursors, one per step
+    int scur[T], snx[T], send = 0;
+    int rcur[T], rnx[T], rend = 0;
+#pragma unroll
+    for (int k = 0; k < T; ++k) { scur[k] = 0; snx[k] = INT_MAX; rcur[k] = 0; rnx[k] = INT_MAX; }
+    if (colv && a.src_ptr != nullptr) {
+        const int lo = a.src_ptr[col];
+        send = a.src_ptr[col + 1];
+        if (lo < send) {
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+                scur[k] = first_at_or_after(a.src_ent, lo, send, X0 - R * (T - 1 - k));
+                snx[k] = scur[k] < send ? a.src_ent[scur[k]].x : INT_MAX;
+            }
+        }
+    }
+    if (own && a.rec_ptr != nullptr) {
+        const int lo = a.rec_ptr[col];
+        rend = a.rec_ptr[col + 1];
+        if (lo < rend) {
+            const int c0 = first_at_or_after(a.rec_ent, lo, rend, X0);
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+                rcur[k] = c0;
+                rnx[k] = c0 < rend ? a.rec_ent[c0].x : INT_MAX;
+            }
+        }
+    }
+
+    if (tid == 0) {
+        for (int s = 0; s < NA + NB; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        *s_abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int j) {
+        const int x0 = xbase + j;
+        const uint32_t ba = smem_u32(&bars[j % NA]);
+        mbar_expect_tx(ba, txA);
+        tma_load3(smem_u32(ringA + (j % NA) * afl), &mapA, ba, zlo - ZH, ylo - R, x0);
+        const uint32_t bb = smem_u32(&bars[NA + j % NB]);
+        float* bs = ringB + (j % NB) * 2 * bfl;
+        mbar_expect_tx(bb, txB);
+        tma_load3(smem_u32(bs), &mapV, bb, zlo, ylo, x0 - R);
+        tma_load3(smem_u32(bs + bfl), &mapK, bb, zlo, ylo, x0 - R);
+    };
+    int issued = 0;
+    if (tid == 0) {
+        for (int j = 0; j < kPrefetch && j < NIT; ++j) issue(j);
+        issued = kPrefetch < NIT ? kPrefetch : NIT;
+    }
+
+    float4 q[T][P];
+#pragma unroll
+    for (int k = 0; k < T; ++k)
+#pragma unroll
+        for (int j = 0; j < P; ++j) q[k][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    bool quit = false;
+    int vslot = 0;  // i % NV
+    for (int i0 = 0; i0 < NIT && !quit; i0 += P) {
+        static_for<P>([&](auto Sc) {
+            constexpr int S = decltype(Sc)::value;
+            const int i = i0 + S;
+            if (i < NIT && !quit) {
+                // kappa of steps k >= 2 at their planes, fetched early (cache hits)
+                float4 kpre[T];
+#pragma unroll
+                for (int k = 1; k < T; ++k) {
+                    const int xk = xbase + i - (k + 1) * R;
+                    kpre[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (colv && xk >= 0 && xk < a.nx && i >= 2 * (k + 1) * R)
+                        kpre[k] = __ldg(reinterpret_cast<const float4*>(a.kap + xk * a.sx + colofs));
+                }
+                bool ok = mbar_wait(smem_u32(&bars[i % NA]), (i / NA) & 1);
+                ok = mbar_wait(smem_u32(&bars[NA + i % NB]), (i / NB) & 1) && ok;
+                if (!ok) {
+                    *s_abort = 1;
+                    atomicOr(a.err, 1);
+                }
+                // publish the centre planes x_k of steps k >= 2
+                if (act) {
+#pragma unroll
+                    for (int k = 1; k < T; ++k)
+                        sts4(planes + ((k - 1) * 2 + (i & 1)) * afl + posA, q[k][(S + R) % P]);
+                }
+                __syncthreads();
+                if (*s_abort) {
+                    if (tid == 0)
+                        for (int j = i; j < issued; ++j) {
+                            mbar_wait(smem_u32(&bars[j % NA]), (j / NA) & 1);
+                            mbar_wait(smem_u32(&bars[NA + j % NB]), (j / NB) & 1);
+                        }
+                    quit = true;
+                    return;
+                }
+                if (tid == 0 && i + kPrefetch < NIT) {
+                    issue(i + kPrefetch);
+                    issued = i + kPrefetch + 1;
+                }
+                if (act) {
+                    const float* pnew = ringA + (i % NA) * afl;
+                    const float* pctr = ringA + ((i - R + NA) % NA) * afl;
+                    const float* pb = ringB + (i % NB) * 2 * bfl;
+                    const int vread = vslot == NV - 1 ? 0 : vslot + 1;  // slot of iteration i - R
+                    float4 prev_u = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 prev_v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < T; ++k) {
+                        // step k+1 of the pass: produces u^{n0+k+1}, v^{n0+k+1/2} at plane xk
+                        q[k][(S + 2 * R) % P] = (k == 0) ? lds4(pnew + posA) : prev_u;
+                        if (k >= 1) vring[((k - 1) * NV + vslot) * blockDim.x + tid] = prev_v;
+                        const int xk = xbase + i - (k + 1) * R;
+                        if (i >= 2 * (k + 1) * R) {
+                            const float* plane = (k == 0) ? pctr : planes + (((k - 1) * 2 + (i & 1)) * afl);
+                            float4 L = laplacian4<R, S>(plane, posA, pitch, q[k], a);
+                            if (xk == snx[k]) {
+                                int c = scur[k];
+                                while (c < send) {
+                                    const int4 e = a.src_ent[c];
+                                    if (e.x != xk) break;
+                                    const float w = __int_as_float(e.w);
+                                    const float qv = a.wavelet[static_cast<long long>(a.n0 + k) * a.nsrc + e.z];
+                                    if (e.y == 0) L.x = __fmaf_rn(w, qv, L.x);
+                                    else if (e.y == 1) L.y = __fmaf_rn(w, qv, L.y);
+                                    else if (e.y == 2) L.z = __fmaf_rn(w, qv, L.z);
+                                    else L.w = __fmaf_rn(w, qv, L.w);
+                                    ++c;
+                                }
+                                scur[k] = c;
+                                snx[k] = c < send ? a.src_ent[c].x : INT_MAX;
+                            }
+                            float4 v = (k == 0) ? lds4(pb + posB) : vring[((k - 1) * NV + vread) * blockDim.x + tid];
+                            const float4 kp = (k == 0) ? lds4(pb + bfl + posB) : kpre[k];
+                            const float dx = (xk >= 0 && xk < a.nx) ? a.damp_x[xk] : 0.f;
+                            float4 u = q[k][(S + R) % P];
+                            update4(L, u, v, kp, dx, dyz, dyz_zero, a.inv2dt);
+                            if (!colv || xk < 0 || xk >= a.nx) {
+                                u = make_float4(0.f, 0.f, 0.f, 0.f);
+                                v = u;
+                            }
+                            if (partial) {
+                                if (gz + 1 >= a.nz) { u.y = 0.f; v.y = 0.f; }
+                                if (gz + 2 >= a.nz) { u.z = 0.f; v.z = 0.f; }
+                                if (gz + 3 >= a.nz) { u.w = 0.f; v.w = 0.f; }
+                            }
+                            if (xk == rnx[k] && xk < X1) {
+                                int c = rcur[k];
+                                while (c < rend) {
+                                    const int2 e = a.rec_ent[c];
+                                    if (e.x != xk) break;
+                                    a.slots[static_cast<long long>(a.n0 + k - a.slot_row0) * a.ntaps + (e.y >> 2)] =
+                                        lane_of(u, e.y & 3);
+                                    ++c;
+                                }
+                                rcur[k] = c;
+                                rnx[k] = c < rend ? a.rec_ent[c].x : INT_MAX;
+                            }
+                            prev_u = u;
+                            prev_v = v;
+                        }
+                    }
+                    // write u^{n+T} and v^{n+T-1/2} of plane x_T
+                    const int xT = xbase + i - T * R;
+                    if (i >= 2 * T * R && own) {
+                        const long long off = xT * a.sx + colofs;
+                        *reinterpret_cast<float4*>(a.out_u + off) = prev_u;
+                        *reinterpret_cast<float4*>(a.out_v + off) = prev_v;
+                    }
+                }
+                vslot = vslot == NV - 1 ? 0 : vslot + 1;
+            }
+        });
+    }
+}
+
+template <int R, int T>
+cudaError_t launch_impl(const CUtensorMap& mapA, const CUtensorMap& mapV, const CUtensorMap& mapK,
+                        const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st)
+{
+    auto fn = pass_kernel<R, T>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    fn<<<static_cast<unsigned>(blocks), threads, smem, st>>>(mapA, mapV, mapK, a);
+    return cudaGetLastError();
+}
+
+}  // namespace detail
+}  // namespace wave

@@ -1,0 +1,196 @@
+"""GPU parity of the forward path (CUDA through the C ABI vs the FP64 oracle).
+
+Bars (FP32 on the GPU, FP64 in the oracle):
+* relative L2 error <= 1e-5 of the final field and of the traces after nt
+  steps, on the same seeded inputs;
+* the time-tiled passes (T > 1) are bit-identical to the one-step kernel
+  (T = 1) -- tiling only reorders independent updates;
+* edge cases: ragged tiles in every axis, nz not a multiple of 4, minimum
+  grids, nt = 0, nt not a multiple of T, several sources on one point,
+  receivers on the grid boundary, no sources, paper's Gaussian initial field.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def W():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1707_02347_gb300 as W
+
+    W.load()
+    return W
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (n if n > 0 else 1.0)
+
+
+def run_gpu(W, w, tiling, u_init=None, want_final=True):
+    dev = torch.device("cuda")
+    m = torch.from_numpy(np.ascontiguousarray(w.m, dtype=np.float32)).to(dev)
+    plan = W.WavePlan(w.shape, w.spacing, w.so, w.dt, w.nt, m, sponge_width=w.sponge_width,
+                      sponge_faces=w.sponge_faces, vmax=w.vmax, tiling=tiling)
+    if len(w.src_xyz):
+        wav = torch.from_numpy(np.ascontiguousarray(w.wavelet, dtype=np.float32)).to(dev)
+        plan.set_sources(w.src_xyz, wav)
+    if len(w.rec_xyz):
+        plan.set_receivers(w.rec_xyz)
+    ui = None if u_init is None else torch.from_numpy(np.ascontiguousarray(u_init, dtype=np.float32)).to(dev)
+    rec, uf = plan.forward(u_init=ui, want_final=want_final)
+    torch.cuda.synchronize()
+    out = (None if rec is None else rec.cpu().numpy(), None if uf is None else uf.cpu().numpy())
+    plan.close()
+    return out
+
+
+def run_oracle(oracle, w, u_init=None):
+    up0 = uc0 = None
+    if u_init is not None:
+        up0, uc0 = (np.asarray(u_init[0], np.float64), np.asarray(u_init[1], np.float64))
+    return oracle.forward(w.shape, w.spacing, w.so, w.dt, w.nt, np.asarray(w.m, np.float64),
+                          src_xyz=w.src_xyz if len(w.src_xyz) else None,
+                          wavelet=w.wavelet if len(w.src_xyz) else None,
+                          rec_xyz=w.rec_xyz if len(w.rec_xyz) else None, u_prev0=up0, u_cur0=uc0,
+                          sponge_width=w.sponge_width, sponge_faces=w.sponge_faces, vmax=w.vmax)
+
+
+def small_layered(shape, so, nt, seed, nrec=9, f=25.0, sponge=6):
+    from paper_1707_02347_gb300 import inputs
+
+    w = inputs.layered_forward(shape, so, nt, seed=seed, f=f, h=10.0, sponge_width=sponge, nrec_line=nrec)
+    # an off-grid second source and a receiver on the far corner face
+    w.src_xyz = np.vstack([w.src_xyz, [[(shape[0] / 3 + 0.37) * 10.0, (shape[1] / 2 - 0.81) * 10.0, 55.5]]])
+    w.wavelet = np.stack([w.wavelet[:, 0], 0.7 * np.roll(w.wavelet[:, 0], 5)], axis=1)
+    w.rec_xyz = np.vstack([w.rec_xyz, [[(shape[0] - 1) * 10.0, (shape[1] - 1) * 10.0, (shape[2] - 1) * 10.0]]])
+    return w
+
+
+def test_plain_forward_64_so4_vs_oracle(W, oracle):
+    from paper_1707_02347_gb300 import inputs
+
+    w = inputs.plain_forward_64(50)
+    rec_o, up_o, uc_o = run_oracle(oracle, w)
+    for tiling in [(1, 16, 64, 64), (2, 32, 32, 64), (4, 24, 24, 64)]:
+        rec, uf = run_gpu(W, w, tiling)
+        assert rel_l2(uf[1], uc_o) <= TOL, tiling
+        assert rel_l2(uf[0], up_o) <= TOL, tiling
+        assert rel_l2(rec, rec_o) <= TOL, tiling
+
+
+@pytest.mark.parametrize("so,shape,tilings", [
+    (4, (37, 34, 30), [(1, 8, 16, 11), (2, 8, 12, 9), (3, 16, 16, 40), (4, 8, 8, 13)]),
+    (8, (41, 35, 38), [(1, 16, 16, 40), (2, 8, 12, 10), (2, 16, 16, 41), (3, 8, 8, 17)]),
+    (16, (36, 33, 34), [(1, 8, 16, 12), (2, 8, 8, 12), (2, 16, 16, 40)]),
+])
+def test_tiled_bit_identical_to_one_step(W, oracle, so, shape, tilings):
+    nt = 23
+    w = small_layered(shape, so, nt, seed=3 + so)
+    ref_rec, ref_u = run_gpu(W, w, tilings[0])
+    rec_o, up_o, uc_o = run_oracle(oracle, w)
+    assert rel_l2(ref_u[1], uc_o) <= TOL
+    assert rel_l2(ref_u[0], up_o) <= TOL
+    assert rel_l2(ref_rec, rec_o) <= TOL
+    for t in tilings[1:]:
+        rec, uf = run_gpu(W, w, t)
+        assert np.array_equal(rec, ref_rec), t
+        assert np.array_equal(uf, ref_u), t
+
+
+def test_layered_so8_long_run_vs_oracle(W, oracle):
+    w = small_layered((64, 56, 60), 8, 300, seed=21, f=20.0, sponge=8)
+    rec_o, up_o, uc_o = run_oracle(oracle, w)
+    rec, uf = run_gpu(W, w, (2, 32, 32, 64))
+    assert rel_l2(uf[1], uc_o) <= TOL
+    assert rel_l2(rec, rec_o) <= TOL
+
+
+def test_gaussian_initial_field_source_free(W, oracle):
+    """Section "Functional Correctness": source removed, u initialised with a
+    3D Gaussian (sigma 0.4 on [-1, 1]^3); tiled vs untiled and vs the oracle."""
+    from paper_1707_02347_gb300 import inputs
+
+    shape = (44, 40, 36)
+    g = inputs.gaussian_field(shape, 0.4)
+    w = inputs.layered_forward(shape, 8, 40, seed=5, f=20.0, h=20.0, sponge_width=0)
+    w.src_xyz = np.zeros((0, 3))
+    w.rec_xyz = np.zeros((0, 3))
+    u0 = np.stack([g, g])
+    _, ref = run_gpu(W, w, (1, 8, 16, 44), u_init=u0)
+    _, up_o, uc_o = run_oracle(oracle, w, u_init=u0)
+    assert rel_l2(ref[1], uc_o) <= TOL
+    for t in [(2, 16, 16, 44), (3, 8, 8, 20)]:
+        _, uf = run_gpu(W, w, t, u_init=u0)
+        assert np.array_equal(uf, ref), t
+
+
+def test_edge_cases(W, oracle):
+    from paper_1707_02347_gb300 import inputs
+
+    # minimum grid (so + 1 per axis), nz not a multiple of 4
+    w = small_layered((9, 9, 9), 8, 7, seed=2, nrec=3, sponge=2)
+    rec_o, up_o, uc_o = run_oracle(oracle, w)
+    for t in [(1, 8, 8, 9), (2, 4, 8, 5), (3, 8, 8, 9)]:
+        rec, uf = run_gpu(W, w, t)
+        assert rel_l2(uf[1], uc_o) <= TOL and rel_l2(rec, rec_o) <= TOL, t
+    # nt = 0: the initial fields come back (u^0 exactly, u^{-1} through one
+    # rounding of the stored increment u^0 - u^{-1}) and there are no traces
+    w0 = small_layered((20, 18, 17), 4, 0, seed=4)
+    rng = np.random.default_rng(0)
+    u0 = rng.standard_normal((2,) + w0.shape).astype(np.float32)
+    rec, uf = run_gpu(W, w0, (2, 8, 8, 20), u_init=u0)
+    assert rec.shape == (0, w0.rec_xyz.shape[0])
+    assert np.array_equal(uf[1], u0[1])
+    np.testing.assert_allclose(uf[0], u0[0], rtol=0, atol=2.5e-7 * np.abs(u0).max())
+    # nt not a multiple of T; two sources on the same grid point
+    w = small_layered((30, 28, 26), 4, 11, seed=7)
+    w.src_xyz = np.vstack([w.src_xyz, w.src_xyz[:1]])
+    w.wavelet = np.concatenate([w.wavelet, -0.5 * w.wavelet[:, :1]], axis=1)
+    rec_o, _, uc_o = run_oracle(oracle, w)
+    r1, u1 = run_gpu(W, w, (1, 8, 8, 30))
+    r3, u3 = run_gpu(W, w, (3, 8, 8, 30))
+    r4, u4 = run_gpu(W, w, (4, 8, 8, 30))
+    assert rel_l2(u1[1], uc_o) <= TOL and rel_l2(r1, rec_o) <= TOL
+    assert np.array_equal(u1, u3) and np.array_equal(r1, r3)
+    assert np.array_equal(u1, u4) and np.array_equal(r1, r4)
+
+
+def test_invalid_arguments(W):
+    dev = torch.device("cuda")
+    m = torch.full((20, 20, 20), 1.0 / 2.25, device=dev)
+    h = (10.0, 10.0, 10.0)
+    dt_max = W.cfl_limit(8, h, 1.5)
+    with pytest.raises(W.WaveError) as e:
+        W.WavePlan((20, 20, 20), h, 8, 1.01 * dt_max, 10, m)
+    assert e.value.status == 2  # WAVE_ERR_CFL
+    with pytest.raises(W.WaveError) as e:
+        W.WavePlan((20, 20, 20), h, 6, 0.5 * dt_max, 10, m)
+    assert e.value.status == 1
+    with pytest.raises(W.WaveError) as e:
+        W.WavePlan((8, 20, 20), h, 8, 0.5 * dt_max, 10, m)
+    assert e.value.status == 1
+    bad = m.clone()
+    bad[3, 4, 5] = -1.0
+    with pytest.raises(W.WaveError) as e:
+        W.WavePlan((20, 20, 20), h, 8, 0.5 * dt_max, 10, bad)
+    assert e.value.status == 1
+    plan = W.WavePlan((20, 20, 20), h, 8, 0.5 * dt_max, 10, m)
+    with pytest.raises(W.WaveError):
+        plan.set_tiling((2, 64, 64, 20))
+    with pytest.raises(W.WaveError):
+        plan.set_tiling((2, 16, 30, 20))
+    plan.set_tiling((2, 16, 16, 20))
+    assert plan.get_tiling() == (2, 16, 16, 20)
+    plan.close()
