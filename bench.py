@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the time-tiled 3D acoustic wave forward path on GB300.
+
+One "step" is one full forward modelling run of the 512^3, SO8, 1000-time-step
+layered workload (seeded synthetic model, 15 Hz Ricker at 20 m depth, 10-cell
+sponge, a line of 512 receivers at 20 m depth whose traces are the result).
+The metric is point-steps per second (GPt/s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU; the per-shot path does not
+shard), launched by torch.distributed.run; rank 0 prints one JSON line.
+--impl reference times the FP64 oracle (the plain C loop nest) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GPt/s (point-steps/s) tiled vs untiled; % HBM roofline; FWI gradient s/shot"
+WORKLOAD = ("tiled forward 512x512x512, h=10 m, SO8, 1000 steps, 20-layer 1.5-4.5 km/s model + seeded 5% "
+            "blurred perturbation (seed 1), 15 Hz Ricker at 20 m depth, 10-cell sponge, 512 receivers at 20 m")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--nt", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-untiled", action="store_true")
+    ap.add_argument("--tiling", default="", help="force T,by,bz,xc instead of autotuning")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        self.gpu_id = gpu_id
+        self.active = False
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    self.samples.append((self.active, parts))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        load = [p for a, p in self.samples if a]
+        if not load:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(p[1]) for p in load if num(p[1]) is not None]
+        smax = [num(p[2]) for p in load if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for p in load for k in range(4) if p[5 + k].lower().startswith("active")})
+        pw = [num(p[3]) for p in load if num(p[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(load), "power_w_max": max(pw) if pw else None}
+
+
+def kernel_traffic(T):
+    """dram bytes per launch of the pass kernel from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    src = os.path.join(ROOT, "paper_1707_02347_gb300", "csrc", "wave_pass.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "tiled_pass_so8_512.md")
+    if not os.path.exists(path):
+        return None, h
+    txt = open(path).read()
+    m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_t = re.search(r"dram_bytes_per_point_T%d:\s*([0-9.eE+-]+)" % T, txt)
+    if not m_h or not m_t or m_h.group(1) != h:
+        return None, h
+    return float(m_t.group(1)), h
+
+
+def run_reference(args, rank):
+    """Time the FP64 oracle on the host cores on a bounded sample: each step is
+    2 time steps of the same 512^3 workload (full grid)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1707_02347_gb300 import inputs
+
+    oracle.build()
+    n = args.grid
+    w = inputs.layered_forward((n, n, n), 8, max(args.nt, 2), seed=1, f=15.0, h=10.0, sponge_width=10,
+                               nrec_line=512)
+    nt_s = 2
+    m64 = w.m.astype(np.float64)
+    cores = os.cpu_count()
+
+    def one():
+        oracle.forward(w.shape, w.spacing, w.so, w.dt, nt_s, m64, src_xyz=w.src_xyz, wavelet=w.wavelet[:nt_s],
+                       rec_xyz=w.rec_xyz, sponge_width=w.sponge_width, sponge_faces=w.sponge_faces, vmax=w.vmax)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t0
+    pts = float(n) ** 3 * nt_s * args.steps
+    val = pts / el / 1e9
+    sample = "%d time steps of the %d^3 SO8 workload per step (full grid, sources and receivers)" % (nt_s, n)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GPt/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": [n, n, n], "so": 8, "nt": args.nt,
+                      "note": "oracle: plain FP64 C loop nest, OpenMP on the outer loop"},
+           "cpu_baseline": {"value": val, "unit": "GPt/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "GPt/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(w):
+    """The oracle as it stands on a bounded sample of the same workload (~10-20 s)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    m64 = w.m.astype(np.float64)
+
+    def run(k):
+        t0 = time.perf_counter()
+        oracle.forward(w.shape, w.spacing, w.so, w.dt, k, m64, src_xyz=w.src_xyz, wavelet=w.wavelet[:k],
+                       rec_xyz=w.rec_xyz, sponge_width=w.sponge_width, sponge_faces=w.sponge_faces, vmax=w.vmax)
+        return time.perf_counter() - t0
+
+    t1 = run(1)
+    k = int(max(1, min(20, 12.0 / max(t1, 1e-3))))
+    tk = run(k)
+    pts = float(np.prod(w.shape)) * k
+    return {"value": pts / tk / 1e9, "unit": "GPt/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d time steps of the full %s SO8 workload (FP64, OpenMP over x), %.1f s" %
+                      (k, "x".join(str(s) for s in w.shape), tk)}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1707_02347_gb300 as W
+    from paper_1707_02347_gb300 import inputs
+
+    W.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = args.grid
+    w = inputs.layered_forward((n, n, n), 8, args.nt, seed=1, f=15.0, h=10.0, sponge_width=10, nrec_line=512)
+    npts = float(n) ** 3
+    stream = torch.cuda.Stream(device=dev)
+    m = torch.from_numpy(w.m).to(dev)
+    wav = torch.from_numpy(w.wavelet.astype(np.float32)).to(dev).contiguous()
+    with torch.cuda.stream(stream):
+        plan = W.WavePlan(w.shape, w.spacing, w.so, w.dt, w.nt, m, sponge_width=w.sponge_width,
+                          sponge_faces=w.sponge_faces, vmax=w.vmax, stream=stream)
+    plan.set_sources(w.src_xyz, wav)
+    plan.set_receivers(w.rec_xyz)
+    # autotune: the best T = 1 (plain one-step) tiling and the best overall
+    if args.tiling:
+        best = tuple(int(x) for x in args.tiling.split(","))
+        plan.set_tiling(best)
+        tuned = []
+    else:
+        tuned = plan.autotune(passes=3)
+        best = plan.get_tiling()
+    if not args.no_untiled:
+        one = [t for t in tuned if t[0][0] == 1]
+        untiled_tiling = min(one, key=lambda c: c[1])[0] if one else (1, 16, 64, 128)
+
+    rec = torch.empty((w.nt, w.rec_xyz.shape[0]), dtype=torch.float32, device=dev)
+    lib = W.load()
+    import ctypes
+
+    def timed(tiling, K, Wm, profile):
+        plan.set_tiling(tiling)
+        for _ in range(Wm):
+            plan.forward(rec_out=rec)
+        lib.wave_profile_read(plan._h, 1, None, None, None, None)
+        lib.wave_profile_enable(plan._h, 1 if profile else 0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            plan.forward(rec_out=rec)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        nl, pms, pst, lau = ctypes.c_longlong(0), ctypes.c_double(0), ctypes.c_double(0), ctypes.c_longlong(0)
+        lib.wave_profile_read(plan._h, 1, ctypes.byref(nl), ctypes.byref(pms), ctypes.byref(pst), ctypes.byref(lau))
+        lib.wave_profile_enable(plan._h, 0)
+        return ms, nl.value, pms.value, pst.value, lau.value
+
+    gpu_uuid = None
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_uuid = u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        gpu_uuid = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+    clk = ClockSampler(gpu_uuid)
+    clk.start()
+    time.sleep(0.5)
+    clk.active = True
+    ms, nl, pass_ms, pass_pts, launches = timed(best, args.steps, args.warmup, True)
+    clk.active = False
+    value = world * args.steps * npts * w.nt / (ms * 1e-3) / 1e9
+    ms_step = ms / args.steps
+
+    untiled = None
+    if not args.no_untiled:
+        ms1, nl1, pms1, pst1, la1 = timed(untiled_tiling, args.steps, args.warmup, True)
+        v1 = world * args.steps * npts * w.nt / (ms1 * 1e-3) / 1e9
+        untiled = {"value": v1, "unit": "GPt/s", "ms_per_step": ms1 / args.steps, "tiling": list(untiled_tiling),
+                   "bytes_per_point_step": 20, "kernel_avg_launch_ms": pms1 / max(nl1, 1),
+                   "speedup_tiled_over_untiled": value / v1}
+    clk.stop()
+
+    hbm, smmax, peak_kind = peaks()
+    T = best[0]
+    bytes_per_launch = 20.0 * npts  # read u, v, kappa; write u, v (once per pass)
+    avg_launch_s = (pass_ms / max(nl, 1)) * 1e-3
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    traffic_pp, src_hash = kernel_traffic(T)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic_pp * npts if traffic_pp is not None else None,
+            "kernel": "pass_kernel<4,%d> (SO8, T=%d)" % (T, T), "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+            "launches_timed": nl, "kernel_source_sha256_16": src_hash}
+    flops_pp = 9 * 4 + 5  # per point-step at SO8: 3 axes x 4 pairs x (add + fma), centre, update
+    fp32_peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
+    roof_alu = {"bound": "alu", "achieved": flops_pp * pass_pts / (pass_ms * 1e-3) / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": flops_pp * pass_pts / (pass_ms * 1e-3) / 1e12 / fp32_peak,
+                "flops_per_point_step": flops_pp,
+                "note": "algorithmic FP32 flops (no halo recompute) vs 152 SMs x 128 lanes x 2 x max clock"}
+
+    e2e = None
+    if not args.no_e2e:
+        m_h = torch.from_numpy(w.m).pin_memory()
+        w_h = torch.from_numpy(w.wavelet.astype(np.float32)).pin_memory()
+        r_h = torch.empty((w.nt, w.rec_xyz.shape[0]), dtype=torch.float32).pin_memory()
+        plan.set_tiling(best)
+        for _ in range(max(1, args.warmup)):
+            plan.forward_host(m_h, w_h, r_h)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.forward_host(m_h, w_h, r_h)
+        barrier()
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * args.steps * npts * w.nt / el / 1e9, "unit": "GPt/s",
+               "h2d_bytes_per_step": int(m_h.numel() * 4 + w_h.numel() * 4),
+               "d2h_bytes_per_step": int(r_h.numel() * 4)}
+        ref_rec = rec.cpu()
+        assert torch.equal(ref_rec, r_h), "host-buffer path differs from the device path"
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "GPt/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "grid": [n, n, n], "so": 8, "nt": w.nt, "tiling": list(best),
+                          "dt_ms": w.dt, "l2": "inputs larger than L2 (each field 537 MB > 129 MB)",
+                          "parallelism": "replicas" if world > 1 else "single GPU"},
+               "untiled": untiled, "roofline": roof, "roofline_alu": roof_alu,
+               "hbm_bound_16B_untiled_gpts": hbm / 16.0,
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+               "autotune": [[list(t), ms_] for t, ms_ in sorted(tuned, key=lambda c: c[1])[:8]]}
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

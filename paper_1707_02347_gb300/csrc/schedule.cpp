@@ -81,19 +81,20 @@ bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std:
 
 wave_tiling default_tiling(const int grid[3], int R, int T)
 {
+    // bank-conflict-free defaults (thread rows of 8 or 16 z quads)
     wave_tiling t{T, 32, 32, 128};
     if (T == 1) {
         t.by = 16;
         t.bz = 64;
     } else if (R == 2) {
-        t.by = 32;
-        t.bz = 32;
+        t.by = 24;
+        t.bz = T == 2 ? 56 : (T == 3 ? 24 : 16);
     } else if (R == 4) {
-        t.by = T == 2 ? 32 : 16;
-        t.bz = T == 2 ? 32 : 24;
+        t.by = T == 2 ? 24 : 16;
+        t.bz = T == 2 ? 24 : 16;
     } else {
         t.by = 16;
-        t.bz = 32;
+        t.bz = 16;
     }
     t.xc = std::min(grid[0], 128);
     return t;
@@ -101,22 +102,29 @@ wave_tiling default_tiling(const int grid[3], int R, int T)
 
 std::vector<wave_tiling> tiling_candidates(const int grid[3], int R)
 {
+    // Shapes whose thread rows span a multiple of 8 z quads (32 floats): a
+    // quarter warp's 128-bit shared loads then never straddle two rows, so
+    // the in-plane reads are free of bank conflicts.  by sets the halo share.
     std::vector<wave_tiling> out;
     const int Tmax = R == 2 ? 4 : (R == 4 ? 3 : 2);
-    const int shapes[][2] = {{8, 64}, {16, 32}, {16, 64}, {24, 24}, {24, 32}, {32, 32}, {32, 64}, {40, 40},
-                             {16, 128}, {48, 32}, {32, 48}};
+    const int bys[] = {8, 12, 16, 20, 24, 32, 40, 48};
     const int slabs[] = {64, 128, 256};
-    for (int T = 1; T <= Tmax; ++T)
-        for (auto& s : shapes)
-            for (int xc : slabs) {
-                wave_tiling t{T, s[0], s[1], std::min(xc, grid[0])};
-                PassGeom g;
-                if (make_geom(grid, R, t, &g, nullptr)) {
+    for (int T = 1; T <= Tmax; ++T) {
+        const int halo = R * (T - 1);
+        for (int bz = 4; bz <= 248; bz += 4) {
+            const int b_cols = round_up(bz + halo, 4) + round_up(halo, 4);
+            if (b_cols % 32 || b_cols > 128) continue;
+            for (int by : bys)
+                for (int xc : slabs) {
+                    wave_tiling t{T, by, bz, std::min(xc, grid[0])};
+                    PassGeom g;
+                    if (!make_geom(grid, R, t, &g, nullptr) || g.threads < 128) continue;
                     bool dup = false;
                     for (auto& o : out) dup = dup || (o.T == t.T && o.by == t.by && o.bz == t.bz && o.xc == t.xc);
                     if (!dup) out.push_back(t);
                 }
-            }
+        }
+    }
     return out;
 }
 

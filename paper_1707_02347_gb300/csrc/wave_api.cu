@@ -115,6 +115,7 @@ struct wave_plan_s {
     float* kap = nullptr;
     float* buf[4] = {nullptr, nullptr, nullptr, nullptr};
     float* damp = nullptr;  // [nx] [ny] [nzp] profiles
+    int dxlo = 0, dxhi = 0;  // x planes without damping along x
     int* err = nullptr;
     int* err_host = nullptr;
     // sources and receivers
@@ -217,6 +218,8 @@ PassArgs base_args(wave_plan_t p, const PassGeom& g, const TapSet& taps, const f
     a.damp_x = p->damp;
     a.damp_y = p->damp + p->n[0];
     a.damp_z = p->damp + p->n[0] + p->n[1];
+    a.dxlo = p->dxlo;
+    a.dxhi = p->dxhi;
     a.inv2dt = static_cast<float>(1.0 / (2.0 * p->dt));
     a.c0 = p->c0;
     for (int k = 0; k < kMaxR; ++k) {
@@ -424,6 +427,10 @@ wave_status set_damping(wave_plan_t p)
         sponge_profile(p->n[a], W, (f >> (2 * a)) & 1, (f >> (2 * a + 1)) & 1, dmax, &prof, a == 2 ? p->nzp : p->n[a]);
         all.insert(all.end(), prof.begin(), prof.end());
     }
+    p->dxlo = 0;
+    while (p->dxlo < p->n[0] && all[p->dxlo] != 0.f) ++p->dxlo;
+    p->dxhi = p->n[0];
+    while (p->dxhi > p->dxlo && all[p->dxhi - 1] != 0.f) --p->dxhi;
     CK(cudaMemcpyAsync(p->damp, all.data(), all.size() * 4, cudaMemcpyHostToDevice, p->st));
     CK(cudaStreamSynchronize(p->st));
     return WAVE_OK;
@@ -454,8 +461,8 @@ void destroy(wave_plan_t p)
 
 wave_status forward_impl(wave_plan_t p, const float* u_init, float* rec_out, float* u_final)
 {
-    if (p->fwd.nsrc > 0 && !p->wavelet) return fail(WAVE_ERR_STATE, "sources set without a wavelet");
-    if (p->fwd.nrec > 0 && !rec_out) return fail(WAVE_ERR_ARG, "rec_out is NULL but receivers are set");
+    if (p->fwd.nsrc > 0 && !p->wavelet && p->nt > 0) return fail(WAVE_ERR_STATE, "sources set without a wavelet");
+    if (p->fwd.nrec > 0 && p->nt > 0 && !rec_out) return fail(WAVE_ERR_ARG, "rec_out is NULL but receivers are set");
     CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
     Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
     if (u_init) {
@@ -472,7 +479,7 @@ wave_status forward_impl(wave_plan_t p, const float* u_init, float* rec_out, flo
     }
     wave_status s = advance(p, &f, p->fwd, p->wavelet, slots, 0, p->nt, true);
     if (s) return s;
-    if (p->fwd.nrec > 0) {
+    if (p->fwd.nrec > 0 && p->nt > 0) {
         if (p->fwd.ntaps > 0)
             CKL(launch_rec_reduce(slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec_out, p->nt, p->fwd.nrec, p->fwd.ntaps,
                                  p->st));
@@ -560,7 +567,9 @@ extern "C" wave_status wave_plan_create(wave_plan_t* out, const int grid[3], con
     fd_weights_exact(so, a);
     const double ih[3] = {1.0 / (spacing[0] * spacing[0]), 1.0 / (spacing[1] * spacing[1]),
                           1.0 / (spacing[2] * spacing[2])};
-    p->c0 = static_cast<float>(a[0] * (ih[0] + ih[1] + ih[2]));
+    // the k = 1 pairs enter the kernel as differences from the centre, so the
+    // centre keeps only the weight of the k >= 2 pairs: a_0 + 2 a_1
+    p->c0 = static_cast<float>((a[0] + 2.0 * a[1]) * (ih[0] + ih[1] + ih[2]));
     for (int k = 1; k <= p->R; ++k) {
         p->cx[k - 1] = static_cast<float>(a[k] * ih[0]);
         p->cy[k - 1] = static_cast<float>(a[k] * ih[1]);

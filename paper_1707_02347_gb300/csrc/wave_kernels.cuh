@@ -26,8 +26,9 @@ struct PassArgs {
     const float* damp_x;    // sponge profile per axis: d(x,y,z) = dx[x] + (dy[y] + dz[z])
     const float* damp_y;
     const float* damp_z;
+    int dxlo, dxhi;         // planes x in [dxlo, dxhi) have dx[x] == 0
     float inv2dt;           // 1 / (2 dt)
-    float c0;               // a_0 (1/hx^2 + 1/hy^2 + 1/hz^2)
+    float c0;               // (a_0 + 2 a_1) (1/hx^2 + 1/hy^2 + 1/hz^2): centre weight of the k >= 2 pairs
     float cx[kMaxR], cy[kMaxR], cz[kMaxR];  // a_k / h^2 per axis
     int n0;                 // time level n at the start of the pass
     // sources: per z-quad column CSR of {x, lane, source, weight bits}, sorted by x

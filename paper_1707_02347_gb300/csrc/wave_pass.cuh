@@ -41,7 +41,8 @@
 //
 // Every arithmetic operation of the point update is an explicit
 // round-to-nearest intrinsic in one fixed order (centre, y pairs, z pairs,
-// x pairs, sources, increment, field), so a pass with T = 1 and passes with
+// x pairs, sources, increment, field; the k = 1 pairs as differences from the
+// centre), so a pass with T = 1 and passes with
 // T > 1 produce bit-identical fields: tiling only reorders independent
 // updates.
 #pragma once
@@ -65,7 +66,12 @@ struct Cfg {
     static constexpr int NA = D + R + 1;          // ring slots of u^n planes
     static constexpr int NB = D + 1;              // ring slots of (v^{n-1/2}, kappa) planes
     static constexpr int NV = R + 1;              // delay slots of the increments (steps >= 2)
-    static constexpr int MAXT = (T * P * 4 > 100) ? 384 : 512;
+    // largest block, chosen so the per-thread register budget (65536 / MAXT,
+    // allocated in groups of 4 warps) holds the T queues of 2r + 1 float4
+    // without spilling
+    static constexpr int MAXT = (R == 2) ? (T <= 3 ? 512 : 384)
+                              : (R == 4) ? (T == 1 ? 512 : (T == 2 ? 384 : 256))
+                                         : (T == 1 ? 384 : 256);
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -150,7 +156,12 @@ __device__ __forceinline__ float lane_of(const float4& v, int l)
 }
 
 // L_h u at the 4 points of a column quad, in the one fixed order every kernel
-// uses: centre, then y pairs k = 1..r, then z pairs, then x pairs.
+// uses: centre, then y pairs k = 1..r, then z pairs, then x pairs.  The
+// k = 1 pairs enter as exact differences (u(+1) - u) + (u(-1) - u); their
+// share of the centre weight is left out of c0.  For a smooth field the
+// centre term and the neighbour sums nearly cancel, and summing the dominant
+// k = 1 pair as differences keeps float32 rounding from swamping L_h u (the
+// differences of neighbouring values are exact).
 // plane: shared-memory plane holding u of this step's input level at the
 // current x with a halo of r rows and ZH columns; pos: the quad's own index;
 // q: the x queue, logical index j at physical (S + j) % P.
@@ -161,15 +172,29 @@ __device__ __forceinline__ float4 laplacian4(const float* plane, int pos, int pi
     constexpr int P = 2 * R + 1;
     constexpr int NQ = ((R + 3) & ~3) / 4;
     const float4 c = q[(S + R) % P];
+    const float cc[4] = {c.x, c.y, c.z, c.w};
     float L[4] = {__fmul_rn(a.c0, c.x), __fmul_rn(a.c0, c.y), __fmul_rn(a.c0, c.z), __fmul_rn(a.c0, c.w)};
+    auto pair = [&](float coef, float m, float p, int l) {
+        return __fmaf_rn(coef, __fadd_rn(m, p), L[l]);
+    };
+    auto pair1 = [&](float coef, float m, float p, int l) {
+        return __fmaf_rn(coef, __fadd_rn(__fsub_rn(m, cc[l]), __fsub_rn(p, cc[l])), L[l]);
+    };
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
         const float4 m = lds4(plane + pos - k * pitch);
         const float4 p = lds4(plane + pos + k * pitch);
-        L[0] = __fmaf_rn(a.cy[k - 1], __fadd_rn(m.x, p.x), L[0]);
-        L[1] = __fmaf_rn(a.cy[k - 1], __fadd_rn(m.y, p.y), L[1]);
-        L[2] = __fmaf_rn(a.cy[k - 1], __fadd_rn(m.z, p.z), L[2]);
-        L[3] = __fmaf_rn(a.cy[k - 1], __fadd_rn(m.w, p.w), L[3]);
+        if (k == 1) {
+            L[0] = pair1(a.cy[0], m.x, p.x, 0);
+            L[1] = pair1(a.cy[0], m.y, p.y, 1);
+            L[2] = pair1(a.cy[0], m.z, p.z, 2);
+            L[3] = pair1(a.cy[0], m.w, p.w, 3);
+        } else {
+            L[0] = pair(a.cy[k - 1], m.x, p.x, 0);
+            L[1] = pair(a.cy[k - 1], m.y, p.y, 1);
+            L[2] = pair(a.cy[k - 1], m.z, p.z, 2);
+            L[3] = pair(a.cy[k - 1], m.w, p.w, 3);
+        }
     }
     float v[4 * (2 * NQ + 1)];
 #pragma unroll
@@ -185,16 +210,24 @@ __device__ __forceinline__ float4 laplacian4(const float* plane, int pos, int pi
     for (int k = 1; k <= R; ++k) {
 #pragma unroll
         for (int l = 0; l < 4; ++l)
-            L[l] = __fmaf_rn(a.cz[k - 1], __fadd_rn(v[4 * NQ + l - k], v[4 * NQ + l + k]), L[l]);
+            L[l] = (k == 1) ? pair1(a.cz[0], v[4 * NQ + l - 1], v[4 * NQ + l + 1], l)
+                            : pair(a.cz[k - 1], v[4 * NQ + l - k], v[4 * NQ + l + k], l);
     }
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
         const float4 m = q[(S + R - k) % P];
         const float4 p = q[(S + R + k) % P];
-        L[0] = __fmaf_rn(a.cx[k - 1], __fadd_rn(m.x, p.x), L[0]);
-        L[1] = __fmaf_rn(a.cx[k - 1], __fadd_rn(m.y, p.y), L[1]);
-        L[2] = __fmaf_rn(a.cx[k - 1], __fadd_rn(m.z, p.z), L[2]);
-        L[3] = __fmaf_rn(a.cx[k - 1], __fadd_rn(m.w, p.w), L[3]);
+        if (k == 1) {
+            L[0] = pair1(a.cx[0], m.x, p.x, 0);
+            L[1] = pair1(a.cx[0], m.y, p.y, 1);
+            L[2] = pair1(a.cx[0], m.z, p.z, 2);
+            L[3] = pair1(a.cx[0], m.w, p.w, 3);
+        } else {
+            L[0] = pair(a.cx[k - 1], m.x, p.x, 0);
+            L[1] = pair(a.cx[k - 1], m.y, p.y, 1);
+            L[2] = pair(a.cx[k - 1], m.z, p.z, 2);
+            L[3] = pair(a.cx[k - 1], m.w, p.w, 3);
+        }
     }
     return make_float4(L[0], L[1], L[2], L[3]);
 }
@@ -272,14 +305,15 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
     const int xbase = X0 - R * T;  // x_0 of iteration 0
     const int ylo = y0 - R * (T - 1), zlo = z0 + a.zlead;
 
-    // thread -> column quad
+    // thread -> column quad.  Columns and planes outside the grid need no
+    // special case: kappa is zero there (TMA zero fill, zero z padding), so
+    // the update keeps u = v = 0 on them -- the zero ghost layer.
     const int tid = threadIdx.x;
     const int nthr = a.qz * a.r1y;
     const bool act = tid < nthr;
     const int ty = act ? tid / a.qz : 0, tq = act ? tid % a.qz : 0;
     const int gy = ylo + ty, gz = zlo + 4 * tq;
     const bool colv = act && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nzp;
-    const bool partial = colv && (gz + 4 > a.nz);
     const bool own = colv && gy >= y0 && gy < y0 + a.by && gz >= z0 && gz < z0 + a.bz;
     const int pitch = a.a_cols;
     const int posA = (ty + R) * pitch + ZH + 4 * tq;
@@ -298,32 +332,28 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
         }
     }
 
-    // source and receiver cursors, one per step
-    int scur[T], snx[T], send = 0;
-    int rcur[T], rnx[T], rend = 0;
+    // sparse events per step: next x with a source or receiver tap in this column
+    int scur[T], rcur[T], nxt[T], send = 0, rend = 0;
 #pragma unroll
-    for (int k = 0; k < T; ++k) { scur[k] = 0; snx[k] = INT_MAX; rcur[k] = 0; rnx[k] = INT_MAX; }
+    for (int k = 0; k < T; ++k) { scur[k] = 0; rcur[k] = 0; nxt[k] = INT_MAX; }
+    // (cursors always start inside the column's own CSR range [lo, end))
     if (colv && a.src_ptr != nullptr) {
         const int lo = a.src_ptr[col];
         send = a.src_ptr[col + 1];
-        if (lo < send) {
 #pragma unroll
-            for (int k = 0; k < T; ++k) {
-                scur[k] = first_at_or_after(a.src_ent, lo, send, X0 - R * (T - 1 - k));
-                snx[k] = scur[k] < send ? a.src_ent[scur[k]].x : INT_MAX;
-            }
+        for (int k = 0; k < T; ++k) {
+            scur[k] = lo < send ? first_at_or_after(a.src_ent, lo, send, X0 - R * (T - 1 - k)) : send;
+            if (scur[k] < send) nxt[k] = a.src_ent[scur[k]].x;
         }
     }
     if (own && a.rec_ptr != nullptr) {
         const int lo = a.rec_ptr[col];
         rend = a.rec_ptr[col + 1];
-        if (lo < rend) {
-            const int c0 = first_at_or_after(a.rec_ent, lo, rend, X0);
+        const int c0 = lo < rend ? first_at_or_after(a.rec_ent, lo, rend, X0) : rend;
 #pragma unroll
-            for (int k = 0; k < T; ++k) {
-                rcur[k] = c0;
-                rnx[k] = c0 < rend ? a.rec_ent[c0].x : INT_MAX;
-            }
+        for (int k = 0; k < T; ++k) {
+            rcur[k] = c0;
+            if (c0 < rend) nxt[k] = min(nxt[k], a.rec_ent[c0].x);
         }
     }
 
@@ -357,122 +387,141 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
 #pragma unroll
         for (int j = 0; j < P; ++j) q[k][j] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    bool quit = false;
-    int vslot = 0;  // i % NV
-    for (int i0 = 0; i0 < NIT && !quit; i0 += P) {
-        static_for<P>([&](auto Sc) {
-            constexpr int S = decltype(Sc)::value;
-            const int i = i0 + S;
-            if (i < NIT && !quit) {
-                // kappa of steps k >= 2 at their planes, fetched early (cache hits)
-                float4 kpre[T];
+    // ring positions of iteration i, advanced incrementally
+    int sA = 0, sAc = NA - R, sB = 0, ph = 0, vslot = 0;  // i % NA, (i - R) % NA, i % NB, parities, i % NV
+    int phA = 0, phB = 0;                                 // (i / NA) & 1, (i / NB) & 1
+    // x of step 0 at iteration 0 is xbase - R; kappa rows of steps >= 1 and the output row follow it
+    const long long sx = a.sx;
+    bool abort = false;
+
+    // One iteration with NACT active steps (compile time) and, if OUTP, the
+    // write of the pass outputs.  Steps k >= NACT are not active yet: their
+    // queues are filled (k == NACT) or untouched (k > NACT).
+    auto body = [&](int i, auto nact_c, auto out_c) {
+        constexpr int NACT = decltype(nact_c)::value;
+        constexpr bool OUTP = decltype(out_c)::value;
+        // kappa of steps k >= 1 at their planes, fetched early (cache hits)
+        float4 kpre[T];
 #pragma unroll
-                for (int k = 1; k < T; ++k) {
-                    const int xk = xbase + i - (k + 1) * R;
-                    kpre[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (colv && xk >= 0 && xk < a.nx && i >= 2 * (k + 1) * R)
-                        kpre[k] = __ldg(reinterpret_cast<const float4*>(a.kap + xk * a.sx + colofs));
-                }
-                bool ok = mbar_wait(smem_u32(&bars[i % NA]), (i / NA) & 1);
-                ok = mbar_wait(smem_u32(&bars[NA + i % NB]), (i / NB) & 1) && ok;
-                if (!ok) {
-                    *s_abort = 1;
-                    atomicOr(a.err, 1);
-                }
-                // publish the centre planes x_k of steps k >= 2
-                if (act) {
-#pragma unroll
-                    for (int k = 1; k < T; ++k)
-                        sts4(planes + ((k - 1) * 2 + (i & 1)) * afl + posA, q[k][(S + R) % P]);
-                }
-                __syncthreads();
-                if (*s_abort) {
-                    if (tid == 0)
-                        for (int j = i; j < issued; ++j) {
-                            mbar_wait(smem_u32(&bars[j % NA]), (j / NA) & 1);
-                            mbar_wait(smem_u32(&bars[NA + j % NB]), (j / NB) & 1);
-                        }
-                    quit = true;
-                    return;
-                }
-                if (tid == 0 && i + kPrefetch < NIT) {
-                    issue(i + kPrefetch);
-                    issued = i + kPrefetch + 1;
-                }
-                if (act) {
-                    const float* pnew = ringA + (i % NA) * afl;
-                    const float* pctr = ringA + ((i - R + NA) % NA) * afl;
-                    const float* pb = ringB + (i % NB) * 2 * bfl;
-                    const int vread = vslot == NV - 1 ? 0 : vslot + 1;  // slot of iteration i - R
-                    float4 prev_u = make_float4(0.f, 0.f, 0.f, 0.f);
-                    float4 prev_v = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int k = 0; k < T; ++k) {
-                        // step k+1 of the pass: produces u^{n0+k+1}, v^{n0+k+1/2} at plane xk
-                        q[k][(S + 2 * R) % P] = (k == 0) ? lds4(pnew + posA) : prev_u;
-                        if (k >= 1) vring[((k - 1) * NV + vslot) * blockDim.x + tid] = prev_v;
-                        const int xk = xbase + i - (k + 1) * R;
-                        if (i >= 2 * (k + 1) * R) {
-                            const float* plane = (k == 0) ? pctr : planes + (((k - 1) * 2 + (i & 1)) * afl);
-                            float4 L = laplacian4<R, S>(plane, posA, pitch, q[k], a);
-                            if (xk == snx[k]) {
-                                int c = scur[k];
-                                while (c < send) {
-                                    const int4 e = a.src_ent[c];
-                                    if (e.x != xk) break;
-                                    const float w = __int_as_float(e.w);
-                                    const float qv = a.wavelet[static_cast<long long>(a.n0 + k) * a.nsrc + e.z];
-                                    if (e.y == 0) L.x = __fmaf_rn(w, qv, L.x);
-                                    else if (e.y == 1) L.y = __fmaf_rn(w, qv, L.y);
-                                    else if (e.y == 2) L.z = __fmaf_rn(w, qv, L.z);
-                                    else L.w = __fmaf_rn(w, qv, L.w);
-                                    ++c;
-                                }
-                                scur[k] = c;
-                                snx[k] = c < send ? a.src_ent[c].x : INT_MAX;
-                            }
-                            float4 v = (k == 0) ? lds4(pb + posB) : vring[((k - 1) * NV + vread) * blockDim.x + tid];
-                            const float4 kp = (k == 0) ? lds4(pb + bfl + posB) : kpre[k];
-                            const float dx = (xk >= 0 && xk < a.nx) ? a.damp_x[xk] : 0.f;
-                            float4 u = q[k][(S + R) % P];
-                            update4(L, u, v, kp, dx, dyz, dyz_zero, a.inv2dt);
-                            if (!colv || xk < 0 || xk >= a.nx) {
-                                u = make_float4(0.f, 0.f, 0.f, 0.f);
-                                v = u;
-                            }
-                            if (partial) {
-                                if (gz + 1 >= a.nz) { u.y = 0.f; v.y = 0.f; }
-                                if (gz + 2 >= a.nz) { u.z = 0.f; v.z = 0.f; }
-                                if (gz + 3 >= a.nz) { u.w = 0.f; v.w = 0.f; }
-                            }
-                            if (xk == rnx[k] && xk < X1) {
-                                int c = rcur[k];
-                                while (c < rend) {
-                                    const int2 e = a.rec_ent[c];
-                                    if (e.x != xk) break;
-                                    a.slots[static_cast<long long>(a.n0 + k - a.slot_row0) * a.ntaps + (e.y >> 2)] =
-                                        lane_of(u, e.y & 3);
-                                    ++c;
-                                }
-                                rcur[k] = c;
-                                rnx[k] = c < rend ? a.rec_ent[c].x : INT_MAX;
-                            }
-                            prev_u = u;
-                            prev_v = v;
-                        }
-                    }
-                    // write u^{n+T} and v^{n+T-1/2} of plane x_T
-                    const int xT = xbase + i - T * R;
-                    if (i >= 2 * T * R && own) {
-                        const long long off = xT * a.sx + colofs;
-                        *reinterpret_cast<float4*>(a.out_u + off) = prev_u;
-                        *reinterpret_cast<float4*>(a.out_v + off) = prev_v;
-                    }
-                }
-                vslot = vslot == NV - 1 ? 0 : vslot + 1;
+        for (int k = 1; k < T; ++k) {
+            kpre[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < NACT) {
+                const int xk = xbase + i - (k + 1) * R;
+                if (colv && xk >= 0 && xk < a.nx)
+                    kpre[k] = __ldg(reinterpret_cast<const float4*>(a.kap + xk * sx + colofs));
             }
-        });
-    }
+        }
+        bool ok = mbar_wait(smem_u32(&bars[sA]), phA);
+        ok = mbar_wait(smem_u32(&bars[NA + sB]), phB) && ok;
+        if (!ok) {
+            *s_abort = 1;
+            atomicOr(a.err, 1);
+        }
+        // publish the centre planes x_k of active steps k >= 1
+        if (act) {
+#pragma unroll
+            for (int k = 1; k < T; ++k)
+                if (k < NACT) sts4(planes + ((k - 1) * 2 + (i & 1)) * afl + posA, q[k][R + 1]);
+        }
+        __syncthreads();
+        if (*s_abort) {
+            if (tid == 0)
+                for (int j = i; j < issued; ++j) {
+                    mbar_wait(smem_u32(&bars[j % NA]), (j / NA) & 1);
+                    mbar_wait(smem_u32(&bars[NA + j % NB]), (j / NB) & 1);
+                }
+            abort = true;
+            return;
+        }
+        if (tid == 0 && i + kPrefetch < NIT) {
+            issue(i + kPrefetch);
+            issued = i + kPrefetch + 1;
+        }
+        if (act) {
+            const float* pnew = ringA + sA * afl;
+            const float* pctr = ringA + sAc * afl;
+            const float* pb = ringB + sB * 2 * bfl;
+            const int vread = vslot == NV - 1 ? 0 : vslot + 1;  // slot of iteration i - R
+            float4 prev_u = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 prev_v = prev_u;
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+                if (k <= NACT) {
+                    // the x queue of step k moves down one plane and takes its newest
+#pragma unroll
+                    for (int j = 0; j + 1 < P; ++j) q[k][j] = q[k][j + 1];
+                    q[k][P - 1] = (k == 0) ? lds4(pnew + posA) : prev_u;
+                    if (k >= 1) vring[((k - 1) * NV + vslot) * blockDim.x + tid] = prev_v;
+                }
+                if (k < NACT) {
+                    // step k+1 of the pass: u^{n0+k+1}, v^{n0+k+1/2} at plane xk
+                    const int xk = xbase + i - (k + 1) * R;
+                    const float* plane = (k == 0) ? pctr : planes + (((k - 1) * 2 + (i & 1)) * afl);
+                    float4 L = laplacian4<R, 0>(plane, posA, pitch, q[k], a);
+                    float4 u = q[k][R];
+                    if (xk == nxt[k]) {
+                        // sources of this plane (before the update) ...
+                        int c = scur[k];
+                        while (c < send) {
+                            const int4 e = a.src_ent[c];
+                            if (e.x != xk) break;
+                            const float w = __int_as_float(e.w);
+                            const float qv = a.wavelet[static_cast<long long>(a.n0 + k) * a.nsrc + e.z];
+                            if (e.y == 0) L.x = __fmaf_rn(w, qv, L.x);
+                            else if (e.y == 1) L.y = __fmaf_rn(w, qv, L.y);
+                            else if (e.y == 2) L.z = __fmaf_rn(w, qv, L.z);
+                            else L.w = __fmaf_rn(w, qv, L.w);
+                            ++c;
+                        }
+                        scur[k] = c;
+                    }
+                    float4 v = (k == 0) ? lds4(pb + posB) : vring[((k - 1) * NV + vread) * blockDim.x + tid];
+                    const float4 kp = (k == 0) ? lds4(pb + bfl + posB) : kpre[k];
+                    const float dx = (xk < a.dxlo || xk >= a.dxhi) ? a.damp_x[min(max(xk, 0), a.nx - 1)] : 0.f;
+                    update4(L, u, v, kp, dx, dyz, dyz_zero, a.inv2dt);
+                    if (xk == nxt[k]) {
+                        // ... and receivers (after it); then the next event of this step
+                        int c = rcur[k];
+                        while (c < rend) {
+                            const int2 e = a.rec_ent[c];
+                            if (e.x != xk) break;
+                            if (xk < X1)
+                                a.slots[static_cast<long long>(a.n0 + k - a.slot_row0) * a.ntaps + (e.y >> 2)] =
+                                    lane_of(u, e.y & 3);
+                            ++c;
+                        }
+                        rcur[k] = c;
+                        int nx2 = INT_MAX;
+                        if (scur[k] < send) nx2 = a.src_ent[scur[k]].x;
+                        if (rcur[k] < rend) nx2 = min(nx2, a.rec_ent[rcur[k]].x);
+                        nxt[k] = nx2;
+                    }
+                    prev_u = u;
+                    prev_v = v;
+                }
+            }
+            if (OUTP && own) {
+                // write u^{n+T} and v^{n+T-1/2} of plane x_T
+                const long long off = (xbase + i - T * R) * sx + colofs;
+                *reinterpret_cast<float4*>(a.out_u + off) = prev_u;
+                *reinterpret_cast<float4*>(a.out_v + off) = prev_v;
+            }
+        }
+        // advance the ring positions
+        vslot = vslot == NV - 1 ? 0 : vslot + 1;
+        if (++sA == NA) { sA = 0; phA ^= 1; }
+        if (++sAc == NA) sAc = 0;
+        if (++sB == NB) { sB = 0; phB ^= 1; }
+    };
+
+    int i = 0;
+    static_for<T>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;  // steps 0 .. k-1 active in this phase
+        const int end = 2 * (k + 1) * R;
+        for (; i < end && !abort; ++i) body(i, std::integral_constant<int, k>{}, std::false_type{});
+    });
+    for (; i < NIT && !abort; ++i) body(i, std::integral_constant<int, T>{}, std::true_type{});
+    (void)ph;
 }
 
 template <int R, int T>

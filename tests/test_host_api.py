@@ -121,8 +121,8 @@ def test_paper_skewed_schedule_order(W):
 
 
 @pytest.mark.parametrize("tiling,ok", [
-    ((2, 32, 32, 128), True), ((2, 64, 64, 128), False), ((2, 32, 30, 128), False), ((9, 32, 32, 64), False),
-    ((1, 16, 64, 128), True), ((3, 16, 24, 128), True), ((3, 24, 24, 128), False),
+    ((2, 16, 56, 128), True), ((2, 32, 32, 128), False), ((2, 64, 64, 128), False), ((2, 32, 30, 128), False),
+    ((9, 32, 32, 64), False), ((1, 16, 64, 128), True), ((3, 16, 16, 128), True), ((3, 24, 24, 128), False),
 ])
 def test_tiling_check_limits(W, tiling, ok):
     assert W.tiling_check((512, 512, 512), 8, tiling) == ok
