@@ -178,6 +178,31 @@ wave_status wave_profile_enable(wave_plan_t plan, int enable);
 wave_status wave_profile_read(wave_plan_t plan, int reset, long long* pass_launches, double* pass_ms,
                               double* point_steps, long long* launches);
 
+/* Receiver sampling that allocates nothing, for callers that cannot allocate
+ * device memory when they need a trace (a fixed memory pool that must not
+ * grow, an allocator that owns the whole device, a real-time loop in which
+ * cudaMalloc may stall).  The paper has no counterpart: this is an interface
+ * of this library only.
+ *
+ * rec[j] = trilinear interpolation of u at xyz[j], the same taps, weights and
+ * summation order as the traces of wave_forward, so sampling the field
+ * wave_forward returns reproduces its last trace row.
+ * grid, spacing: host [3] (cells, metres); u: device [nx][ny][nz] float32;
+ * xyz: host [nrec][3] metres; rec: device [nrec] float32, written on `stream`
+ * (a cudaStream_t, NULL = legacy default stream); nothing is synchronised.
+ * At most 65536 receivers per call (WAVE_ERR_ARG beyond that).
+ *
+ * The tap slots live in one static device array (5.75 MiB, held by every GPU
+ * that loads the library until the process exits).  Every call shares it and
+ * writes every slot it reads, so no state carries over between calls, but
+ * calls that overlap on the GPU (other streams, other host threads) race.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+wave_status wave_sample_noalloc(const int grid[3], const double spacing[3], const float* u, int nrec,
+                                const double* xyz, float* rec, void* stream);
+
 /* Destroy the plan and free its device memory.  NULL is accepted. */
 wave_status wave_plan_destroy(wave_plan_t plan);
 
