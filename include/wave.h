@@ -53,13 +53,16 @@ typedef enum {
 typedef struct wave_plan_s* wave_plan_t;
 
 /* Tiling of one pass (a "tile schedule"):
- *   T  : time steps per pass over HBM (1 = the plain one-step method);
- *   by : output tile extent along y (points);
- *   bz : output tile extent along z (points, multiple of 4);
- *   xc : extent along x of the slab one thread block streams through.
- * Every field 0 = let the library choose (autotuner or built-in default). */
+ *   T      : time steps per pass over HBM (1 = the plain one-step method);
+ *   by     : output tile extent along y (points);
+ *   bz     : output tile extent along z (points, multiple of 4);
+ *   xc     : extent along x of the slab one thread block streams through;
+ *   unroll : how the per-column queue of planes along x rotates, 0 = register
+ *            moves in a compact loop, 1 = loop unrolled over the queue length.
+ * (T, by, bz, unroll) must name a compiled kernel variant (wave_tiling_check).
+ * Fields T, by, bz, xc of 0 = let the library choose. */
 typedef struct {
-    int T, by, bz, xc;
+    int T, by, bz, xc, unroll;
 } wave_tiling;
 
 typedef struct {
@@ -203,11 +206,39 @@ wave_status wave_profile_read(wave_plan_t plan, int reset, long long* pass_launc
 wave_status wave_sample_noalloc(const int grid[3], const double spacing[3], const float* u, int nrec,
                                 const double* xyz, float* rec, void* stream);
 
+/* ---- batched shots ---------------------------------------------------------
+ * Many independent shots (plans with their own grid, SO, tiling, sources and
+ * receivers, as the autotuner chose per shot) advanced together: the whole
+ * time loop of every shot is captured into one CUDA graph, each shot on a
+ * stream of its own, and replayed with a single graph launch.  The plans
+ * must live on one device and stay alive as long as the batch. */
+typedef struct wave_batch_s* wave_batch_t;
+
+wave_status wave_batch_create(wave_batch_t* out, int nplans, const wave_plan_t* plans);
+
+/* Forward modelling of every shot from zero fields, the same results as
+ * wave_forward per plan (bit-identical).  rec_out: host array of nplans
+ * device pointers ([nt_i][nrec_i] each; may be NULL for shots without
+ * receivers).  The graph is captured on the first call and again when the
+ * rec_out pointers change.  Synchronises `stream` (cudaStream_t) and
+ * reports device-side timeouts. */
+wave_status wave_batch_forward(wave_batch_t batch, float* const* rec_out, void* stream);
+
+wave_status wave_batch_destroy(wave_batch_t batch);
+
 /* Destroy the plan and free its device memory.  NULL is accepted. */
 wave_status wave_plan_destroy(wave_plan_t plan);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* wave_last_error(void);
+
+/* Self-test of failure detection: launches one thread block that waits,
+ * with the pass kernel's bounded-wait helper and a limit of limit_ms (0 <
+ * limit_ms <= 10000), on an mbarrier phase that never completes.  Returns
+ * WAVE_ERR_TIMEOUT when the wait gave up and the block returned (the
+ * expected outcome: the device stays usable), WAVE_OK if the wait was
+ * satisfied (a defect).  Runs on the current device; synchronises it. */
+wave_status wave_selftest_timeout(double limit_ms);
 
 /* ---- tile-legality scheduler (host only, no GPU) --------------------------
  * Chapter "Time-Tiling" / Section "Skewing Dependencies": a stencil update

@@ -21,7 +21,7 @@ from . import build as _build
 
 __all__ = [
     "WaveError", "load", "fd_weights", "cfl_limit", "skew_factor", "tiling_check", "schedule_verify",
-    "schedule_verify_custom", "skewed_order_legal", "WavePlan", "FWIGradient", "STATUS",
+    "schedule_verify_custom", "skewed_order_legal", "WavePlan", "WaveBatch", "FWIGradient", "STATUS",
 ]
 
 STATUS = {0: "WAVE_OK", 1: "WAVE_ERR_ARG", 2: "WAVE_ERR_CFL", 3: "WAVE_ERR_OOM", 4: "WAVE_ERR_CUDA",
@@ -35,10 +35,11 @@ class WaveError(RuntimeError):
 
 
 class Tiling(ctypes.Structure):
-    _fields_ = [("T", ctypes.c_int), ("by", ctypes.c_int), ("bz", ctypes.c_int), ("xc", ctypes.c_int)]
+    _fields_ = [("T", ctypes.c_int), ("by", ctypes.c_int), ("bz", ctypes.c_int), ("xc", ctypes.c_int),
+                ("unroll", ctypes.c_int)]
 
     def as_tuple(self):
-        return (self.T, self.by, self.bz, self.xc)
+        return (self.T, self.by, self.bz, self.xc, self.unroll)
 
 
 class Options(ctypes.Structure):
@@ -93,6 +94,14 @@ def load(build_if_missing: bool = True):
             "wave_schedule_verify_custom": (st, [_I3, ctypes.c_int, ctypes.POINTER(Tiling), ctypes.c_int,
                                                  ctypes.c_int]),
             "wave_skewed_order_legal": (ctypes.c_int, [ctypes.c_int] * 6),
+            "wave_batch_create": (st, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]),
+            "wave_batch_forward": (st, [_VP, ctypes.POINTER(_VP), _VP]),
+            "wave_batch_destroy": (st, [_VP]),
+            "wave_selftest_timeout": (st, [ctypes.c_double]),
+            "wave_profile_enable": (st, [_VP, ctypes.c_int]),
+            "wave_profile_read": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -130,8 +139,8 @@ def skew_factor(so: int) -> int:
 def _tiling(t) -> Tiling:
     if isinstance(t, Tiling):
         return t
-    T, by, bz, xc = (tuple(t) + (0, 0, 0, 0))[:4]
-    return Tiling(int(T), int(by), int(bz), int(xc))
+    T, by, bz, xc, unroll = (tuple(t) + (0, 0, 0, 0, 0))[:5]
+    return Tiling(int(T), int(by), int(bz), int(xc), int(unroll))
 
 
 def tiling_check(grid, so: int, tiling) -> bool:
@@ -290,6 +299,40 @@ class WavePlan:
         _check(self._lib.wave_gradient(self._h, _dev_ptr(d_obs, "d_obs"), _dev_ptr(grad_out, "grad_m"),
                                        ctypes.byref(J), int(checkpoint_every)))
         return J.value, grad_out
+
+
+class WaveBatch:
+    """Several plans (shots) advanced together: one CUDA graph holding every
+    shot's time loop, one stream per shot, one graph launch per call."""
+
+    def __init__(self, plans):
+        self._lib = load()
+        self.plans = list(plans)
+        arr = (_VP * len(self.plans))(*[p._h for p in self.plans])
+        h = _VP()
+        _check(self._lib.wave_batch_create(ctypes.byref(h), len(self.plans), arr))
+        self._h = h
+
+    def forward(self, recs=None):
+        """recs: one CUDA tensor [nt, nrec] per plan (allocated if None)."""
+        torch = _torch()
+        if recs is None:
+            recs = [torch.empty((p.nt, p.nrec), dtype=torch.float32, device=p.device) if p.nrec else None
+                    for p in self.plans]
+        ptrs = (_VP * len(self.plans))(*[None if r is None else r.data_ptr() for r in recs])
+        _check(self._lib.wave_batch_forward(self._h, ptrs, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return recs
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.wave_batch_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _make_fwi_function():

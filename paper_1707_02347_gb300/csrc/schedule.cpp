@@ -35,15 +35,14 @@ static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 int padded_nz(int nz) { return round_up(nz, 4); }
 
-bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std::string* why)
+bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std::string* why, bool need_kernel)
 {
     auto no = [&](const std::string& s) {
         if (why) *why = s;
         return false;
     };
     if (R != 2 && R != 4 && R != 8) return no("space order must be 4, 8 or 16");
-    const int maxT = pass_max_threads(R, t.T);
-    if (t.T < 1 || maxT <= 0) return no("no kernel for T = " + std::to_string(t.T) + " at SO " + std::to_string(2 * R));
+    if (t.T < 1) return no("T must be >= 1");
     if (t.by < 1) return no("tile by must be >= 1");
     if (t.bz < 4 || t.bz % 4) return no("tile bz must be a positive multiple of 4");
     if (t.xc < 1) return no("slab xc must be >= 1");
@@ -64,11 +63,13 @@ bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std:
     G.a_rows = G.r1y + 2 * R;
     G.a_cols = G.b_cols + 2 * ZH;
     G.threads = G.qz * G.r1y;
-    G.block = round_up(G.threads, 32);
-    if (G.block > maxT)
-        return no("tile needs " + std::to_string(G.block) + " threads, kernel allows " + std::to_string(maxT));
-    if (G.a_cols > 256 || G.a_rows > 256) return no("staged box exceeds the TMA limit of 256 per dimension");
-    G.smem = pass_smem_bytes(R, t.T, G.a_rows, G.a_cols, G.b_rows, G.b_cols, G.block);
+    G.block = G.threads;
+    G.shape = find_pass_shape(R, t.T, G.qz, G.r1y, t.unroll);
+    if (!G.shape && need_kernel)
+        return no("no compiled kernel for SO " + std::to_string(2 * R) + ", T = " + std::to_string(t.T) +
+                  " with " + std::to_string(G.r1y) + " thread rows of " + std::to_string(G.qz) + " z quads" +
+                  (t.unroll ? " (unrolled)" : ""));
+    G.smem = G.shape ? G.shape->smem : 0;
     if (G.smem > 227 * 1024) return no("tile needs " + std::to_string(G.smem) + " bytes of shared memory");
     G.nty = (ny + t.by - 1) / t.by;
     G.ntz = (nzp + t.bz - 1) / t.bz;
@@ -79,50 +80,49 @@ bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std:
     return true;
 }
 
+// The compiled shape (qz, r1y) as an output tile (by, bz) for radius R and T.
+static bool shape_tile(int R, int T, int qz, int ry, int* by, int* bz)
+{
+    const int halo = R * (T - 1);
+    *by = ry - 2 * halo;
+    // largest bz (multiple of 4) with round_up(bz + halo, 4) + round_up(halo, 4) == 4 qz
+    *bz = 0;
+    for (int b = 4; b <= 4 * qz; b += 4)
+        if (round_up(b + halo, 4) + round_up(halo, 4) == 4 * qz) *bz = b;
+    return *by >= 1 && *bz >= 4;
+}
+
 wave_tiling default_tiling(const int grid[3], int R, int T)
 {
-    // bank-conflict-free defaults (thread rows of 8 or 16 z quads)
-    wave_tiling t{T, 32, 32, 128};
-    if (T == 1) {
-        t.by = 16;
-        t.bz = 64;
-    } else if (R == 2) {
-        t.by = 24;
-        t.bz = T == 2 ? 56 : (T == 3 ? 24 : 16);
-    } else if (R == 4) {
-        t.by = T == 2 ? 24 : 16;
-        t.bz = T == 2 ? 24 : 16;
-    } else {
-        t.by = 16;
-        t.bz = 16;
-    }
-    t.xc = std::min(grid[0], 128);
-    return t;
+    // the first compiled shape of (R, T) (bank-conflict-free: rows of 8, 16 or 32 quads)
+    wave_tiling t{T, 0, 0, std::min(grid[0], 128), 0};
+    int n = 0;
+    const PassShape* s = pass_shapes(&n);
+    for (int i = 0; i < n; ++i)
+        if (s[i].R == R && s[i].T == T && s[i].unroll == 0 && shape_tile(R, T, s[i].qz, s[i].ry, &t.by, &t.bz))
+            return t;
+    return wave_tiling{T, 0, 0, 0, 0};
 }
 
 std::vector<wave_tiling> tiling_candidates(const int grid[3], int R)
 {
-    // Shapes whose thread rows span a multiple of 8 z quads (32 floats): a
-    // quarter warp's 128-bit shared loads then never straddle two rows, so
-    // the in-plane reads are free of bank conflicts.  by sets the halo share.
+    // every compiled shape of radius R, with three slab lengths
     std::vector<wave_tiling> out;
-    const int Tmax = R == 2 ? 4 : (R == 4 ? 3 : 2);
-    const int bys[] = {8, 12, 16, 20, 24, 32, 40, 48};
+    int n = 0;
+    const PassShape* s = pass_shapes(&n);
     const int slabs[] = {64, 128, 256};
-    for (int T = 1; T <= Tmax; ++T) {
-        const int halo = R * (T - 1);
-        for (int bz = 4; bz <= 248; bz += 4) {
-            const int b_cols = round_up(bz + halo, 4) + round_up(halo, 4);
-            if (b_cols % 32 || b_cols > 128) continue;
-            for (int by : bys)
-                for (int xc : slabs) {
-                    wave_tiling t{T, by, bz, std::min(xc, grid[0])};
-                    PassGeom g;
-                    if (!make_geom(grid, R, t, &g, nullptr) || g.threads < 128) continue;
-                    bool dup = false;
-                    for (auto& o : out) dup = dup || (o.T == t.T && o.by == t.by && o.bz == t.bz && o.xc == t.xc);
-                    if (!dup) out.push_back(t);
-                }
+    for (int i = 0; i < n; ++i) {
+        if (s[i].R != R) continue;
+        int by, bz;
+        if (!shape_tile(R, s[i].T, s[i].qz, s[i].ry, &by, &bz)) continue;
+        for (int xc : slabs) {
+            wave_tiling t{s[i].T, by, bz, std::min(xc, grid[0]), s[i].unroll};
+            PassGeom g;
+            if (!make_geom(grid, R, t, &g, nullptr)) continue;
+            bool dup = false;
+            for (auto& o : out)
+                dup = dup || (o.T == t.T && o.by == t.by && o.bz == t.bz && o.xc == t.xc && o.unroll == t.unroll);
+            if (!dup) out.push_back(t);
         }
     }
     return out;
@@ -146,7 +146,7 @@ static bool verify_schedule(const int grid[3], int R, const wave_tiling& t, int 
                             std::string* why)
 {
     PassGeom g;
-    if (!make_geom(grid, R, t, &g, why)) return false;
+    if (!make_geom(grid, R, t, &g, why, false)) return false;
     const int nx = grid[0], ny = grid[1], nz = grid[2];
     const int T = t.T;
     // geometry under test: the thread region carries halo_per_step (T-1) rows

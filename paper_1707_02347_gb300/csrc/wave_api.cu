@@ -265,8 +265,8 @@ wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const
         }
         CK(cudaEventRecord(p->ev[p->ev_used], p->st));
     }
-    if (!launch_pass(p->R, g.T, *mA, *mV, *mK, a, g.block, g.smem, g.blocks, p->st, &e))
-        return fail(WAVE_ERR_ARG, "no kernel for this (SO, T)");
+    if (!g.shape) return fail(WAVE_ERR_ARG, "no compiled kernel for this tile shape");
+    e = g.shape->launch(*mA, *mV, *mK, a, g.block, g.smem, g.blocks, p->st);
     p->launches++;
     if (p->prof) {
         CK(cudaEventRecord(p->ev[p->ev_used + 1], p->st));
@@ -390,6 +390,7 @@ wave_tiling fill_tiling(wave_plan_t p, wave_tiling t)
     if (t.bz <= 0) t.bz = d.bz;
     if (t.xc <= 0) t.xc = d.xc;
     t.T = T;
+    t.unroll = t.unroll ? 1 : 0;
     return t;
 }
 
@@ -912,6 +913,148 @@ extern "C" wave_status wave_profile_read(wave_plan_t p, int reset, long long* pa
         p->prof_points = 0.0;
         p->launches = 0;
     }
+    return WAVE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched shots: every plan's whole time loop captured into one CUDA graph,
+// one stream per shot (forked from and joined back into the capture stream),
+// replayed with a single graph launch.
+// ---------------------------------------------------------------------------
+
+struct wave_batch_s {
+    std::vector<wave_plan_t> plans;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    std::vector<float*> recs;  // rec_out pointers the graph was captured with
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int dev = 0;
+};
+
+namespace {
+
+void batch_release_graph(wave_batch_t b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Capture forward_impl of every plan; plan i runs on streams[i].
+wave_status batch_capture(wave_batch_t b, float* const* rec_out)
+{
+    const size_t n = b->plans.size();
+    for (size_t i = 0; i < n; ++i) {
+        wave_plan_t p = b->plans[i];
+        if (p->fwd.nsrc > 0 && !p->wavelet && p->nt > 0) return fail(WAVE_ERR_STATE, "a shot has no wavelet");
+        if (p->fwd.nrec > 0 && p->nt > 0 && (!rec_out || !rec_out[i]))
+            return fail(WAVE_ERR_ARG, "wave_batch_forward: a shot with receivers has no rec_out");
+        // everything forward_impl would allocate is allocated before the capture
+        if (p->fwd.nrec > 0 && p->fwd.ntaps > 0) {
+            wave_status s = ensure_slots(p, static_cast<size_t>(p->nt) * p->fwd.ntaps);
+            if (s) return s;
+        }
+    }
+    batch_release_graph(b);
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    wave_status st = WAVE_OK;
+    CK(cudaEventRecord(b->events[n], b->cap));
+    for (size_t i = 0; i < n && !st; ++i) {
+        wave_plan_t p = b->plans[i];
+        cudaStream_t keep = p->st;
+        p->st = b->streams[i];
+        cudaError_t e = cudaStreamWaitEvent(p->st, b->events[n], 0);
+        if (e != cudaSuccess) st = check_cuda("cudaStreamWaitEvent", e);
+        if (!st) st = forward_impl(p, nullptr, rec_out ? rec_out[i] : nullptr, nullptr);
+        if (!st) {
+            e = cudaEventRecord(b->events[i], p->st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->events[i], 0);
+            if (e != cudaSuccess) st = check_cuda("event join", e);
+        }
+        p->st = keep;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return check_cuda("cudaStreamEndCapture", e);
+    b->graph = g;
+    CK(cudaGraphInstantiate(&b->exec, g, 0));
+    b->recs.assign(rec_out ? rec_out : nullptr, rec_out ? rec_out + n : nullptr);
+    return WAVE_OK;
+}
+
+}  // namespace
+
+extern "C" wave_status wave_batch_create(wave_batch_t* out, int nplans, const wave_plan_t* plans)
+{
+    if (!out || nplans < 1 || !plans) return fail(WAVE_ERR_ARG, "wave_batch_create: bad argument");
+    *out = nullptr;
+    for (int i = 0; i < nplans; ++i)
+        if (!plans[i]) return fail(WAVE_ERR_ARG, "wave_batch_create: null plan");
+    const int dev = plans[0]->dev;
+    for (int i = 0; i < nplans; ++i)
+        if (plans[i]->dev != dev) return fail(WAVE_ERR_ARG, "wave_batch_create: plans on different devices");
+    DeviceGuard g(dev);
+    auto* b = new wave_batch_s();
+    b->dev = dev;
+    b->plans.assign(plans, plans + nplans);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    for (int i = 0; i < nplans && e == cudaSuccess; ++i) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->streams.push_back(s);
+    }
+    for (int i = 0; i <= nplans && e == cudaSuccess; ++i) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->events.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        wave_batch_destroy(b);
+        return check_cuda("wave_batch_create", e);
+    }
+    *out = b;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_batch_forward(wave_batch_t b, float* const* rec_out, void* stream)
+{
+    if (!b) return fail(WAVE_ERR_ARG, "wave_batch_forward: null batch");
+    DeviceGuard g(b->dev);
+    const size_t n = b->plans.size();
+    bool same = b->exec && b->recs.size() == (rec_out ? n : 0);
+    for (size_t i = 0; same && rec_out && i < n; ++i) same = b->recs[i] == rec_out[i];
+    if (!same) {
+        wave_status s = batch_capture(b, rec_out);
+        if (s) return s;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (auto* p : b->plans) CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+    CK(cudaGraphLaunch(b->exec, st));
+    CK(cudaStreamSynchronize(st));
+    for (auto* p : b->plans) {
+        CK(cudaMemcpy(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (*p->err_host) return fail(WAVE_ERR_TIMEOUT, "a bounded device-side wait gave up in a batched shot");
+    }
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_batch_destroy(wave_batch_t b)
+{
+    if (!b) return WAVE_OK;
+    DeviceGuard g(b->dev);
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    batch_release_graph(b);
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    for (auto e : b->events) cudaEventDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
     return WAVE_OK;
 }
 

@@ -25,8 +25,9 @@ struct PassGeom {
     int nty = 0, ntz = 0, nxs = 0;
     int qz = 0, r1y = 0, zlead = 0;
     int a_rows = 0, a_cols = 0, b_rows = 0, b_cols = 0;
-    int threads = 0;         // threads doing work (qz * r1y)
-    int block = 0;           // launched block size (multiple of 32)
+    int threads = 0;         // threads of a block (qz * r1y, whole warps)
+    int block = 0;           // launched block size (= threads)
+    const struct PassShape* shape = nullptr;  // the compiled instantiation
     long long blocks = 0;
     size_t smem = 0;
 };
@@ -34,7 +35,9 @@ struct PassGeom {
 int padded_nz(int nz);
 // Fill g for (grid, R, tiling); false with a reason if the tiling is not legal
 // for the kernel (limits, alignment, TMA box sizes, shared memory).
-bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std::string* why);
+// need_kernel = false checks the schedule geometry only (no compiled shape needed).
+bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std::string* why,
+               bool need_kernel = true);
 // Built-in default tiling for a grid, radius and T.
 wave_tiling default_tiling(const int grid[3], int R, int T);
 // Candidate tilings for the autotuner.

@@ -2,20 +2,14 @@
 // the dispatcher of the pipelined pass kernel (wave_pass.cuh).
 #include "wave_kernels.cuh"
 
+#include <mutex>
+#include <vector>
+
 namespace wave {
 
-bool launch_pass_r2(int T, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const PassArgs&, int, size_t,
-                    long long, cudaStream_t, cudaError_t*);
-bool launch_pass_r4(int T, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const PassArgs&, int, size_t,
-                    long long, cudaStream_t, cudaError_t*);
-bool launch_pass_r8(int T, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const PassArgs&, int, size_t,
-                    long long, cudaStream_t, cudaError_t*);
-int pass_max_threads_r2(int T);
-int pass_max_threads_r4(int T);
-int pass_max_threads_r8(int T);
-int pass_prefetch_r2(int T);
-int pass_prefetch_r4(int T);
-int pass_prefetch_r8(int T);
+const PassShape* pass_shapes_r2(int* n);
+const PassShape* pass_shapes_r4(int* n);
+const PassShape* pass_shapes_r8(int* n);
 
 namespace {
 // ---------------------------------------------------------------------------
@@ -167,46 +161,28 @@ unsigned grid_for(long long n, int threads)
 
 }  // namespace
 
-int pass_max_threads(int R, int T)
+const PassShape* pass_shapes(int* count)
 {
-    switch (R) {
-        case 2: return pass_max_threads_r2(T);
-        case 4: return pass_max_threads_r4(T);
-        case 8: return pass_max_threads_r8(T);
-        default: return 0;
-    }
+    static std::vector<PassShape> all;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (auto fn : {pass_shapes_r2, pass_shapes_r4, pass_shapes_r8}) {
+            int n = 0;
+            const PassShape* s = fn(&n);
+            all.insert(all.end(), s, s + n);
+        }
+    });
+    *count = static_cast<int>(all.size());
+    return all.data();
 }
 
-static int pass_prefetch(int R, int T)
+const PassShape* find_pass_shape(int R, int T, int qz, int ry, int unroll)
 {
-    switch (R) {
-        case 2: return pass_prefetch_r2(T);
-        case 4: return pass_prefetch_r4(T);
-        case 8: return pass_prefetch_r8(T);
-        default: return 0;
-    }
-}
-
-size_t pass_smem_bytes(int R, int T, int a_rows, int a_cols, int b_rows, int b_cols, int block)
-{
-    const int D = pass_prefetch(R, T);
-    const size_t NA = D + R + 1, NB = D + 1, NV = R + 1;
-    const size_t abytes = (static_cast<size_t>(a_rows) * a_cols * 4 + 127) & ~static_cast<size_t>(127);
-    const size_t bbytes = (static_cast<size_t>(b_rows) * b_cols * 4 + 127) & ~static_cast<size_t>(127);
-    const size_t hdr = (8 * (NA + NB) + 4 + 127) & ~static_cast<size_t>(127);
-    return hdr + NA * abytes + NB * 2 * bbytes + 2 * static_cast<size_t>(T - 1) * abytes +
-           static_cast<size_t>(T - 1) * NV * static_cast<size_t>(block) * 16;
-}
-
-bool launch_pass(int R, int T, const CUtensorMap& mapA, const CUtensorMap& mapP, const CUtensorMap& mapK,
-                 const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st, cudaError_t* err)
-{
-    switch (R) {
-        case 2: return launch_pass_r2(T, mapA, mapP, mapK, a, threads, smem, blocks, st, err);
-        case 4: return launch_pass_r4(T, mapA, mapP, mapK, a, threads, smem, blocks, st, err);
-        case 8: return launch_pass_r8(T, mapA, mapP, mapK, a, threads, smem, blocks, st, err);
-        default: return false;
-    }
+    int n = 0;
+    const PassShape* s = pass_shapes(&n);
+    for (int i = 0; i < n; ++i)
+        if (s[i].R == R && s[i].T == T && s[i].qz == qz && s[i].ry == ry && s[i].unroll == unroll) return &s[i];
+    return nullptr;
 }
 
 cudaError_t launch_kappa(const float* m, float* kap, int nx, int ny, int nz, int nzp, float dt2, cudaStream_t st)

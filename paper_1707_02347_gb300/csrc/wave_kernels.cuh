@@ -45,18 +45,21 @@ struct PassArgs {
     int* err;               // device error word (bit 0: a bounded wait gave up)
 };
 
-// Launch one pass with R = so/2 and T steps from the state (u^n, v^{n-1/2})
-// (mapA over u^n, mapV over v^{n-1/2}, mapK over kappa).  Returns false if the
-// (R, T) pair has no instantiation.
-bool launch_pass(int R, int T, const CUtensorMap& mapA, const CUtensorMap& mapP, const CUtensorMap& mapK,
-                 const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st,
-                 cudaError_t* err);
+// One compiled instantiation of the pass kernel: radius R, T steps, thread
+// blocks of `ry` rows by `qz` z quads, its shared memory and its launcher.
+struct PassShape {
+    int R, T, qz, ry;
+    int unroll;  // x-queue rotation: 0 = register moves, 1 = loop unrolled over the queue length
+    size_t smem;
+    cudaError_t (*launch)(const CUtensorMap& mapA, const CUtensorMap& mapV, const CUtensorMap& mapK,
+                          const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st);
+};
 
-// Largest thread block the (R, T) instantiation was compiled for.
-int pass_max_threads(int R, int T);
-
-// Shared memory bytes of a pass with this geometry.
-size_t pass_smem_bytes(int R, int T, int a_rows, int a_cols, int b_rows, int b_cols, int block);
+// Every compiled shape (wave_pass_r*.cu), and the one matching (R, T, qz, ry)
+// or nullptr.  A pass runs from the state (u^n, v^{n-1/2}): mapA over u^n,
+// mapV over v^{n-1/2}, mapK over kappa.
+const PassShape* pass_shapes(int* count);
+const PassShape* find_pass_shape(int R, int T, int qz, int ry, int unroll);
 
 // Elementwise helpers.
 cudaError_t launch_kappa(const float* m, float* kap, int nx, int ny, int nz, int nzp, float dt2, cudaStream_t st);

@@ -66,12 +66,20 @@ struct Cfg {
     static constexpr int NA = D + R + 1;          // ring slots of u^n planes
     static constexpr int NB = D + 1;              // ring slots of (v^{n-1/2}, kappa) planes
     static constexpr int NV = R + 1;              // delay slots of the increments (steps >= 2)
-    // largest block, chosen so the per-thread register budget (65536 / MAXT,
-    // allocated in groups of 4 warps) holds the T queues of 2r + 1 float4
-    // without spilling
-    static constexpr int MAXT = (R == 2) ? (T <= 3 ? 512 : 384)
-                              : (R == 4) ? (T == 1 ? 512 : (T == 2 ? 384 : 256))
-                                         : (T == 1 ? 384 : 256);
+};
+
+// Compile-time geometry of a thread block: RY rows of QZ z quads; the staged
+// u^n box adds r rows and ZH columns on each side.
+template <int R, int T, int QZ, int RY>
+struct Geo {
+    static constexpr int ZH = Cfg<R, T>::ZH;
+    static constexpr int NTHR = QZ * RY;
+    static constexpr int B_COLS = 4 * QZ, B_ROWS = RY;
+    static constexpr int A_COLS = B_COLS + 2 * ZH, A_ROWS = RY + 2 * R;
+    static constexpr int AFL = (A_ROWS * A_COLS + 31) & ~31;  // floats per u^n slot (128-byte aligned)
+    static constexpr int BFL = (B_ROWS * B_COLS + 31) & ~31;  // floats per v or kappa plane
+    static_assert(NTHR % 32 == 0, "whole warps");
+    static_assert(A_COLS <= 256 && A_ROWS <= 256, "TMA box limit");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -114,15 +122,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for phase `parity` of an mbarrier, giving up after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Wait for phase `parity` of an mbarrier, giving up after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs)
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         for (int k = 0; k < 64; ++k)
             if (mbar_try(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -233,18 +242,19 @@ __device__ __forceinline__ float4 laplacian4(const float* plane, int pos, int pi
 }
 
 // New increment of one point: ((1 - g) v + kappa L) / (1 + g), g = d kappa / (2 dt).
-// With g == 0 both branches give the same bits ((1 - 0) v is v, x / 1 is x),
-// so the branch taken never changes a result.
+// With g == 0 this is bit-identical to fma(kappa, L, v): (1 - 0) v is v and
+// x / 1 is x, so whether a warp takes the damped or the undamped branch never
+// changes a result.
 __device__ __forceinline__ float increment(float L, float v, float kap, float g)
 {
-    if (g == 0.f) return __fmaf_rn(kap, L, v);
     return __fdiv_rn(__fmaf_rn(kap, L, __fmaf_rn(-g, v, v)), __fadd_rn(1.f, g));
 }
 
 __device__ __forceinline__ void update4(const float4& L, float4& u, float4& v, const float4& kap, float dx,
                                         const float (&dyz)[4], bool dyz_zero, float inv2dt)
 {
-    if (dx == 0.f && dyz_zero) {
+    // warp-uniform: the damped path only where some lane of the warp is in the sponge
+    if (!__any_sync(0xffffffffu, !(dx == 0.f && dyz_zero))) {
         v.x = __fmaf_rn(kap.x, L.x, v.x);
         v.y = __fmaf_rn(kap.y, L.y, v.y);
         v.z = __fmaf_rn(kap.z, L.z, v.z);
@@ -272,26 +282,25 @@ __device__ __forceinline__ int first_at_or_after(const E* ent, int lo, int hi, i
     return lo;
 }
 
-template <int R, int T>
-__global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
+template <int R, int T, int QZ, int RY, bool ROT>
+__global__ void __launch_bounds__(QZ * RY, 1)
     pass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
                 const __grid_constant__ CUtensorMap mapK, const PassArgs a)
 {
     using C = Cfg<R, T>;
+    using G = Geo<R, T, QZ, RY>;
     constexpr int P = C::P, NA = C::NA, NB = C::NB, NV = C::NV, ZH = C::ZH, kPrefetch = C::D;
+    constexpr int afl = G::AFL, bfl = G::BFL, pitch = G::A_COLS, NTHR = G::NTHR;
+    constexpr uint32_t hdr = (8u * (NA + NB) + 4u + 127u) & ~127u;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     volatile int* s_abort = reinterpret_cast<volatile int*>(smem + 8 * (NA + NB));
-    const uint32_t abytes = (static_cast<uint32_t>(a.a_rows * a.a_cols * 4) + 127u) & ~127u;
-    const uint32_t bbytes = (static_cast<uint32_t>(a.b_rows * a.b_cols * 4) + 127u) & ~127u;
-    const uint32_t hdr = (8u * (NA + NB) + 4u + 127u) & ~127u;
     float* ringA = reinterpret_cast<float*>(smem + hdr);
-    float* ringB = reinterpret_cast<float*>(smem + hdr + NA * abytes);
-    float* planes = reinterpret_cast<float*>(smem + hdr + NA * abytes + NB * 2 * bbytes);
-    float4* vring = reinterpret_cast<float4*>(smem + hdr + NA * abytes + NB * 2 * bbytes + 2 * (T - 1) * abytes);
-    const uint32_t txA = static_cast<uint32_t>(a.a_rows * a.a_cols * 4);
-    const uint32_t txB = static_cast<uint32_t>(2 * a.b_rows * a.b_cols * 4);
-    const int afl = static_cast<int>(abytes / 4), bfl = static_cast<int>(bbytes / 4);
+    float* ringB = ringA + NA * afl;
+    float* planes = ringB + NB * 2 * bfl;
+    float4* vring = reinterpret_cast<float4*>(planes + 2 * (T - 1) * afl);
+    constexpr uint32_t txA = static_cast<uint32_t>(G::A_ROWS * G::A_COLS * 4);
+    constexpr uint32_t txB = static_cast<uint32_t>(2 * G::B_ROWS * G::B_COLS * 4);
 
     // thread block -> tile (z fastest, then y, then x slab)
     long long blk = blockIdx.x;
@@ -309,15 +318,13 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
     // special case: kappa is zero there (TMA zero fill, zero z padding), so
     // the update keeps u = v = 0 on them -- the zero ghost layer.
     const int tid = threadIdx.x;
-    const int nthr = a.qz * a.r1y;
-    const bool act = tid < nthr;
-    const int ty = act ? tid / a.qz : 0, tq = act ? tid % a.qz : 0;
+    constexpr bool act = true;  // every thread of the block owns a column quad
+    const int ty = tid / QZ, tq = tid % QZ;
     const int gy = ylo + ty, gz = zlo + 4 * tq;
-    const bool colv = act && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nzp;
+    const bool colv = gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nzp;
     const bool own = colv && gy >= y0 && gy < y0 + a.by && gz >= z0 && gz < z0 + a.bz;
-    const int pitch = a.a_cols;
     const int posA = (ty + R) * pitch + ZH + 4 * tq;
-    const int posB = ty * a.b_cols + 4 * tq;
+    const int posB = ty * G::B_COLS + 4 * tq;
     const long long colofs = static_cast<long long>(colv ? gy : 0) * a.nzp + (colv ? gz : 0);
     const int col = colv ? gy * (a.nzp >> 2) + (gz >> 2) : 0;
 
@@ -397,9 +404,15 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
     // One iteration with NACT active steps (compile time) and, if OUTP, the
     // write of the pass outputs.  Steps k >= NACT are not active yet: their
     // queues are filled (k == NACT) or untouched (k > NACT).
-    auto body = [&](int i, auto nact_c, auto out_c) {
+    // rot_c: -1 = the queues move down one slot per iteration (register moves);
+    // S >= 0 = the loop is unrolled over the queue length and logical slot j
+    // lives at register (S + j) % P, so the rotation costs nothing.
+    auto body = [&](int i, auto nact_c, auto out_c, auto rot_c) {
         constexpr int NACT = decltype(nact_c)::value;
         constexpr bool OUTP = decltype(out_c)::value;
+        constexpr int SR = decltype(rot_c)::value;
+        constexpr int S = SR < 0 ? 0 : SR;
+        constexpr bool MOVE = SR < 0;
         // kappa of steps k >= 1 at their planes, fetched early (cache hits)
         float4 kpre[T];
 #pragma unroll
@@ -421,7 +434,7 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
         if (act) {
 #pragma unroll
             for (int k = 1; k < T; ++k)
-                if (k < NACT) sts4(planes + ((k - 1) * 2 + (i & 1)) * afl + posA, q[k][R + 1]);
+                if (k < NACT) sts4(planes + ((k - 1) * 2 + (i & 1)) * afl + posA, q[k][MOVE ? R + 1 : (S + R) % P]);
         }
         __syncthreads();
         if (*s_abort) {
@@ -448,17 +461,19 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
             for (int k = 0; k < T; ++k) {
                 if (k <= NACT) {
                     // the x queue of step k moves down one plane and takes its newest
+                    if (MOVE) {
 #pragma unroll
-                    for (int j = 0; j + 1 < P; ++j) q[k][j] = q[k][j + 1];
-                    q[k][P - 1] = (k == 0) ? lds4(pnew + posA) : prev_u;
-                    if (k >= 1) vring[((k - 1) * NV + vslot) * blockDim.x + tid] = prev_v;
+                        for (int j = 0; j + 1 < P; ++j) q[k][j] = q[k][j + 1];
+                    }
+                    q[k][(S + 2 * R) % P] = (k == 0) ? lds4(pnew + posA) : prev_u;
+                    if (k >= 1) vring[((k - 1) * NV + vslot) * NTHR + tid] = prev_v;
                 }
                 if (k < NACT) {
                     // step k+1 of the pass: u^{n0+k+1}, v^{n0+k+1/2} at plane xk
                     const int xk = xbase + i - (k + 1) * R;
                     const float* plane = (k == 0) ? pctr : planes + (((k - 1) * 2 + (i & 1)) * afl);
-                    float4 L = laplacian4<R, 0>(plane, posA, pitch, q[k], a);
-                    float4 u = q[k][R];
+                    float4 L = laplacian4<R, S>(plane, posA, pitch, q[k], a);
+                    float4 u = q[k][(S + R) % P];
                     if (xk == nxt[k]) {
                         // sources of this plane (before the update) ...
                         int c = scur[k];
@@ -475,7 +490,7 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
                         }
                         scur[k] = c;
                     }
-                    float4 v = (k == 0) ? lds4(pb + posB) : vring[((k - 1) * NV + vread) * blockDim.x + tid];
+                    float4 v = (k == 0) ? lds4(pb + posB) : vring[((k - 1) * NV + vread) * NTHR + tid];
                     const float4 kp = (k == 0) ? lds4(pb + bfl + posB) : kpre[k];
                     const float dx = (xk < a.dxlo || xk >= a.dxhi) ? a.damp_x[min(max(xk, 0), a.nx - 1)] : 0.f;
                     update4(L, u, v, kp, dx, dyz, dyz_zero, a.inv2dt);
@@ -514,21 +529,44 @@ __global__ void __launch_bounds__(Cfg<R, T>::MAXT, 1)
         if (++sB == NB) { sB = 0; phB ^= 1; }
     };
 
+    using NoRot = std::integral_constant<int, -1>;
     int i = 0;
     static_for<T>([&](auto kc) {
         constexpr int k = decltype(kc)::value;  // steps 0 .. k-1 active in this phase
         const int end = 2 * (k + 1) * R;
-        for (; i < end && !abort; ++i) body(i, std::integral_constant<int, k>{}, std::false_type{});
+        for (; i < end && !abort; ++i) body(i, std::integral_constant<int, k>{}, std::false_type{}, NoRot{});
     });
-    for (; i < NIT && !abort; ++i) body(i, std::integral_constant<int, T>{}, std::true_type{});
+    if (ROT) {
+        // steady state unrolled over the queue length; the queues enter it in
+        // the moved layout, which is rotation 0
+        for (int i0 = i; i0 < NIT && !abort; i0 += P)
+            static_for<P>([&](auto sc) {
+                constexpr int S = decltype(sc)::value;
+                if (i0 + S < NIT && !abort)
+                    body(i0 + S, std::integral_constant<int, T>{}, std::true_type{}, std::integral_constant<int, S>{});
+            });
+    } else {
+        for (; i < NIT && !abort; ++i) body(i, std::integral_constant<int, T>{}, std::true_type{}, NoRot{});
+    }
     (void)ph;
 }
 
-template <int R, int T>
+// Shared memory of the (R, T, QZ, RY) instantiation.
+template <int R, int T, int QZ, int RY>
+constexpr size_t smem_bytes()
+{
+    using C = Cfg<R, T>;
+    using G = Geo<R, T, QZ, RY>;
+    return ((8u * (C::NA + C::NB) + 4u + 127u) & ~127u) +
+           4u * (static_cast<size_t>(C::NA) * G::AFL + 2u * C::NB * G::BFL + 2u * (T - 1) * G::AFL) +
+           16u * static_cast<size_t>(T - 1) * C::NV * G::NTHR;
+}
+
+template <int R, int T, int QZ, int RY, bool ROT>
 cudaError_t launch_impl(const CUtensorMap& mapA, const CUtensorMap& mapV, const CUtensorMap& mapK,
                         const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st)
 {
-    auto fn = pass_kernel<R, T>;
+    auto fn = pass_kernel<R, T, QZ, RY, ROT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     fn<<<static_cast<unsigned>(blocks), threads, smem, st>>>(mapA, mapV, mapK, a);

@@ -53,7 +53,7 @@ def problem(seed=3, shape=(34, 30, 28), so=8, nt=90):
                 sponge=dict(sponge_width=5, sponge_faces=0b101111), rng=rng)
 
 
-def plan_for(W, P, m, tiling=(2, 16, 16, 34)):
+def plan_for(W, P, m, tiling=(2, 24, 24, 34)):
     dev = torch.device("cuda")
     mt = torch.from_numpy(np.ascontiguousarray(m, np.float32)).to(dev)
     plan = W.WavePlan(P["shape"], P["h"], P["so"], P["dt"], P["nt"], mt, vmax=P["vmax"], tiling=tiling,

@@ -29,7 +29,7 @@ def _run_forward(W, shape, nt, seed, nrec):
     dev = torch.device("cuda")
     m = torch.from_numpy(np.ascontiguousarray(w.m)).to(dev)
     plan = W.WavePlan(shape, w.spacing, 8, w.dt, nt, m, sponge_width=w.sponge_width, vmax=w.vmax,
-                      tiling=(2, 16, 24, 40))
+                      tiling=(2, 16, 56, 40))
     plan.set_sources(w.src_xyz, torch.from_numpy(w.wavelet.astype(np.float32)).to(dev))
     plan.set_receivers(w.rec_xyz)
     rec, uf = plan.forward(want_final=True)
