@@ -164,13 +164,23 @@ __device__ __forceinline__ float lane_of(const float4& v, int l)
     return l == 0 ? v.x : (l == 1 ? v.y : (l == 2 ? v.z : v.w));
 }
 
+// Packed float32 pairs (sm_100+: one instruction, two IEEE round-to-nearest
+// operations, each bit-identical to its scalar counterpart).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float c, float2 x, float2 acc) { return __ffma2_rn(make_float2(c, c), x, acc); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
 // L_h u at the 4 points of a column quad, in the one fixed order every kernel
 // uses: centre, then y pairs k = 1..r, then z pairs, then x pairs.  The
 // k = 1 pairs enter as exact differences (u(+1) - u) + (u(-1) - u); their
 // share of the centre weight is left out of c0.  For a smooth field the
 // centre term and the neighbour sums nearly cancel, and summing the dominant
 // k = 1 pair as differences keeps float32 rounding from swamping L_h u (the
-// differences of neighbouring values are exact).
+// differences of neighbouring values are exact).  Lanes 0-1 and 2-3 are
+// computed as packed pairs.
 // plane: shared-memory plane holding u of this step's input level at the
 // current x with a halo of r rows and ZH columns; pos: the quad's own index;
 // q: the x queue, logical index j at physical (S + j) % P.
@@ -181,29 +191,25 @@ __device__ __forceinline__ float4 laplacian4(const float* plane, int pos, int pi
     constexpr int P = 2 * R + 1;
     constexpr int NQ = ((R + 3) & ~3) / 4;
     const float4 c = q[(S + R) % P];
-    const float cc[4] = {c.x, c.y, c.z, c.w};
-    float L[4] = {__fmul_rn(a.c0, c.x), __fmul_rn(a.c0, c.y), __fmul_rn(a.c0, c.z), __fmul_rn(a.c0, c.w)};
-    auto pair = [&](float coef, float m, float p, int l) {
-        return __fmaf_rn(coef, __fadd_rn(m, p), L[l]);
-    };
-    auto pair1 = [&](float coef, float m, float p, int l) {
-        return __fmaf_rn(coef, __fadd_rn(__fsub_rn(m, cc[l]), __fsub_rn(p, cc[l])), L[l]);
+    const float2 cl = lo2(c), ch = hi2(c);
+    const float2 ncl = neg2(cl), nch = neg2(ch);
+    float2 Ll = __fmul2_rn(make_float2(a.c0, a.c0), cl);
+    float2 Lh = __fmul2_rn(make_float2(a.c0, a.c0), ch);
+    // one neighbour pair (m, p) of coefficient coef into both halves
+    auto pair = [&](float coef, const float4& m, const float4& p, bool diff) {
+        if (diff) {
+            Ll = fma2(coef, add2(add2(lo2(m), ncl), add2(lo2(p), ncl)), Ll);
+            Lh = fma2(coef, add2(add2(hi2(m), nch), add2(hi2(p), nch)), Lh);
+        } else {
+            Ll = fma2(coef, add2(lo2(m), lo2(p)), Ll);
+            Lh = fma2(coef, add2(hi2(m), hi2(p)), Lh);
+        }
     };
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
         const float4 m = lds4(plane + pos - k * pitch);
         const float4 p = lds4(plane + pos + k * pitch);
-        if (k == 1) {
-            L[0] = pair1(a.cy[0], m.x, p.x, 0);
-            L[1] = pair1(a.cy[0], m.y, p.y, 1);
-            L[2] = pair1(a.cy[0], m.z, p.z, 2);
-            L[3] = pair1(a.cy[0], m.w, p.w, 3);
-        } else {
-            L[0] = pair(a.cy[k - 1], m.x, p.x, 0);
-            L[1] = pair(a.cy[k - 1], m.y, p.y, 1);
-            L[2] = pair(a.cy[k - 1], m.z, p.z, 2);
-            L[3] = pair(a.cy[k - 1], m.w, p.w, 3);
-        }
+        pair(a.cy[k - 1], m, p, k == 1);
     }
     float v[4 * (2 * NQ + 1)];
 #pragma unroll
@@ -217,28 +223,14 @@ __device__ __forceinline__ float4 laplacian4(const float* plane, int pos, int pi
     v[4 * NQ + 0] = c.x; v[4 * NQ + 1] = c.y; v[4 * NQ + 2] = c.z; v[4 * NQ + 3] = c.w;
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
-#pragma unroll
-        for (int l = 0; l < 4; ++l)
-            L[l] = (k == 1) ? pair1(a.cz[0], v[4 * NQ + l - 1], v[4 * NQ + l + 1], l)
-                            : pair(a.cz[k - 1], v[4 * NQ + l - k], v[4 * NQ + l + k], l);
+        constexpr int o = 4 * NQ;
+        const float4 m = make_float4(v[o - k], v[o + 1 - k], v[o + 2 - k], v[o + 3 - k]);
+        const float4 p = make_float4(v[o + k], v[o + 1 + k], v[o + 2 + k], v[o + 3 + k]);
+        pair(a.cz[k - 1], m, p, k == 1);
     }
 #pragma unroll
-    for (int k = 1; k <= R; ++k) {
-        const float4 m = q[(S + R - k) % P];
-        const float4 p = q[(S + R + k) % P];
-        if (k == 1) {
-            L[0] = pair1(a.cx[0], m.x, p.x, 0);
-            L[1] = pair1(a.cx[0], m.y, p.y, 1);
-            L[2] = pair1(a.cx[0], m.z, p.z, 2);
-            L[3] = pair1(a.cx[0], m.w, p.w, 3);
-        } else {
-            L[0] = pair(a.cx[k - 1], m.x, p.x, 0);
-            L[1] = pair(a.cx[k - 1], m.y, p.y, 1);
-            L[2] = pair(a.cx[k - 1], m.z, p.z, 2);
-            L[3] = pair(a.cx[k - 1], m.w, p.w, 3);
-        }
-    }
-    return make_float4(L[0], L[1], L[2], L[3]);
+    for (int k = 1; k <= R; ++k) pair(a.cx[k - 1], q[(S + R - k) % P], q[(S + R + k) % P], k == 1);
+    return make_float4(Ll.x, Ll.y, Lh.x, Lh.y);
 }
 
 // New increment of one point: ((1 - g) v + kappa L) / (1 + g), g = d kappa / (2 dt).
@@ -255,20 +247,18 @@ __device__ __forceinline__ void update4(const float4& L, float4& u, float4& v, c
 {
     // warp-uniform: the damped path only where some lane of the warp is in the sponge
     if (!__any_sync(0xffffffffu, !(dx == 0.f && dyz_zero))) {
-        v.x = __fmaf_rn(kap.x, L.x, v.x);
-        v.y = __fmaf_rn(kap.y, L.y, v.y);
-        v.z = __fmaf_rn(kap.z, L.z, v.z);
-        v.w = __fmaf_rn(kap.w, L.w, v.w);
+        const float2 vl = __ffma2_rn(lo2(kap), lo2(L), lo2(v));
+        const float2 vh = __ffma2_rn(hi2(kap), hi2(L), hi2(v));
+        v = make_float4(vl.x, vl.y, vh.x, vh.y);
     } else {
         v.x = increment(L.x, v.x, kap.x, __fmul_rn(__fmul_rn(__fadd_rn(dx, dyz[0]), kap.x), inv2dt));
         v.y = increment(L.y, v.y, kap.y, __fmul_rn(__fmul_rn(__fadd_rn(dx, dyz[1]), kap.y), inv2dt));
         v.z = increment(L.z, v.z, kap.z, __fmul_rn(__fmul_rn(__fadd_rn(dx, dyz[2]), kap.z), inv2dt));
         v.w = increment(L.w, v.w, kap.w, __fmul_rn(__fmul_rn(__fadd_rn(dx, dyz[3]), kap.w), inv2dt));
     }
-    u.x = __fadd_rn(u.x, v.x);
-    u.y = __fadd_rn(u.y, v.y);
-    u.z = __fadd_rn(u.z, v.z);
-    u.w = __fadd_rn(u.w, v.w);
+    const float2 ul = __fadd2_rn(lo2(u), lo2(v));
+    const float2 uh = __fadd2_rn(hi2(u), hi2(v));
+    u = make_float4(ul.x, ul.y, uh.x, uh.y);
 }
 
 // First CSR entry of [lo, hi) whose x is >= x0.
@@ -282,8 +272,11 @@ __device__ __forceinline__ int first_at_or_after(const E* ent, int lo, int hi, i
     return lo;
 }
 
+// One-step kernels keep at least 512 threads resident per SM (their single
+// x-queue fits in 128 registers); T > 1 kernels may use the whole register
+// file for their queues.
 template <int R, int T, int QZ, int RY, bool ROT>
-__global__ void __launch_bounds__(QZ * RY, 1)
+__global__ void __launch_bounds__(QZ * RY, (T == 1 && QZ * RY < 512) ? 512 / (QZ * RY) : 1)
     pass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
                 const __grid_constant__ CUtensorMap mapK, const PassArgs a)
 {
