@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-untiled", action="store_true")
     ap.add_argument("--tiling", default="", help="force T,by,bz,xc[,unroll] instead of autotuning")
-    ap.add_argument("--workload", choices=["tiled512", "so16", "batched"], default="tiled512",
+    ap.add_argument("--so", type=int, default=8, help="space order of the tiled512 workload (4, 8 or 16)")
+    ap.add_argument("--workload", choices=["tiled512", "so16", "batched", "gradient"], default="tiled512",
                     help="tiled512: the headline 512^3 SO8 run; so16: 768x768x384 SO16 with 501x501 "
                          "surface receivers; batched: 24 uneven SO4/SO8 shots in one graph launch")
     return ap.parse_args()
@@ -258,6 +259,53 @@ def run_batched(args, W, inputs, dev, world, rank, dist):
         p.close()
 
 
+def run_gradient(args, W, inputs, dev, world, rank, dist):
+    """FWI gradient of one shot: 256^3, SO8, 800 steps, 10 Hz Ricker, 256
+    receivers on a line at 20 m; data from the seeded true model (seed 3),
+    gradient on the true model blurred with sigma = 10 cells, checkpoints
+    every 40 steps.  Seconds per shot (forward + checkpoints + recompute +
+    adjoint + imaging condition)."""
+    import numpy as np
+    import torch
+
+    from paper_1707_02347_gb300 import replicas
+
+    n, nt = 256, min(args.nt, 800)
+    w = inputs.layered_forward((n, n, n), 8, nt, seed=3, f=10.0, h=10.0, sponge_width=10, nrec_line=256)
+    v_true = 1.0 / np.sqrt(w.m.astype(np.float64))
+    v0 = inputs.gaussian_blur(v_true.astype(np.float32), 10.0) / inputs.gaussian_blur(np.ones(w.shape, np.float32), 10.0)
+    m_true = torch.from_numpy(w.m).to(dev)
+    m0 = torch.from_numpy(inputs.slowness2(v0)).to(dev)
+    plan = W.WavePlan(w.shape, w.spacing, 8, w.dt, nt, m_true, sponge_width=w.sponge_width, vmax=w.vmax)
+    plan.set_sources(w.src_xyz, torch.from_numpy(w.wavelet.astype(np.float32)).to(dev))
+    plan.set_receivers(w.rec_xyz)
+    plan.autotune(passes=2)
+    d_obs, _ = plan.forward()
+    d_obs = d_obs.clone()
+    plan.set_model(m0)
+    for _ in range(max(args.warmup, 1)):
+        J, g = plan.gradient(d_obs, checkpoint_every=40)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        J, g = plan.gradient(d_obs, checkpoint_every=40)
+    torch.cuda.synchronize()
+    el = replicas.max_over_ranks(time.perf_counter() - t0, dev)
+    if rank == 0:
+        out = {"metric": "FWI gradient s/shot", "value": el / args.steps, "unit": "s/shot", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+               "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": "FWI gradient 256x256x256, h=10 m, SO8, %d steps, 10 Hz Ricker, 256 receivers "
+                                      "at 20 m, true model seed 3, start = true blurred sigma 10, checkpoint "
+                                      "every 40 steps" % nt, "tiling": list(plan.get_tiling()), "misfit": J,
+                          "point_steps_per_s": float(n) ** 3 * nt / (el / args.steps)}}
+        print(json.dumps(out), flush=True)
+    plan.close()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -290,6 +338,9 @@ def main():
     if args.workload == "batched":
         run_batched(args, W, inputs, dev, world, rank, dist)
         return
+    if args.workload == "gradient":
+        run_gradient(args, W, inputs, dev, world, rank, dist)
+        return
     n = args.grid
     if args.workload == "so16":
         w = inputs.high_order_forward(nt=min(args.nt, 500))
@@ -297,9 +348,10 @@ def main():
                          "(seed 2), 501x501 surface receivers at 25 m (trilinear)" % w.nt)
         so = 16
     else:
-        w = inputs.layered_forward((n, n, n), 8, args.nt, seed=1, f=15.0, h=10.0, sponge_width=10, nrec_line=512)
-        workload_name = WORKLOAD
-        so = 8
+        so = args.so
+        w = inputs.layered_forward((n, n, n), so, args.nt, seed=1, f=15.0, h=10.0, sponge_width=10, nrec_line=512)
+        workload_name = WORKLOAD if so == 8 and n == 512 else WORKLOAD.replace("SO8", "SO%d" % so).replace(
+            "512x512x512", "%dx%dx%d" % (n, n, n))
     npts = float(np.prod(w.shape))
     stream = torch.cuda.Stream(device=dev)
     m = torch.from_numpy(w.m).to(dev)
