@@ -57,8 +57,10 @@ typedef struct wave_plan_s* wave_plan_t;
  *   by     : output tile extent along y (points);
  *   bz     : output tile extent along z (points, multiple of 4);
  *   xc     : extent along x of the slab one thread block streams through;
- *   unroll : how the per-column queue of planes along x rotates, 0 = register
- *            moves in a compact loop, 1 = loop unrolled over the queue length.
+ *   unroll : where the per-column queue of planes along x lives and how it
+ *            advances: 0 = registers, moved in a compact loop; 1 = registers,
+ *            loop unrolled over the queue length; 2 = tensor memory (a ring
+ *            per warp, read back with tcgen05.ld; no register queue).
  * (T, by, bz, unroll) must name a compiled kernel variant (wave_tiling_check).
  * Fields T, by, bz, xc of 0 = let the library choose. */
 typedef struct {

@@ -221,11 +221,11 @@ PassArgs base_args(wave_plan_t p, const PassGeom& g, const TapSet& taps, const f
     a.dxlo = p->dxlo;
     a.dxhi = p->dxhi;
     a.inv2dt = static_cast<float>(1.0 / (2.0 * p->dt));
-    a.c0 = p->c0;
+    a.c0 = make_float2(p->c0, p->c0);
     for (int k = 0; k < kMaxR; ++k) {
-        a.cx[k] = p->cx[k];
-        a.cy[k] = p->cy[k];
-        a.cz[k] = p->cz[k];
+        a.cx[k] = make_float2(p->cx[k], p->cx[k]);
+        a.cy[k] = make_float2(p->cy[k], p->cy[k]);
+        a.cz[k] = make_float2(p->cz[k], p->cz[k]);
     }
     a.src_ptr = taps.nsrc ? taps.src_ptr : nullptr;
     a.src_ent = taps.src_ent;
@@ -390,7 +390,7 @@ wave_tiling fill_tiling(wave_plan_t p, wave_tiling t)
     if (t.bz <= 0) t.bz = d.bz;
     if (t.xc <= 0) t.xc = d.xc;
     t.T = T;
-    t.unroll = t.unroll ? 1 : 0;
+    if (t.unroll < 0) t.unroll = 0;
     return t;
 }
 

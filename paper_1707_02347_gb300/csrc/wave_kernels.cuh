@@ -28,8 +28,8 @@ struct PassArgs {
     const float* damp_z;
     int dxlo, dxhi;         // planes x in [dxlo, dxhi) have dx[x] == 0
     float inv2dt;           // 1 / (2 dt)
-    float c0;               // (a_0 + 2 a_1) (1/hx^2 + 1/hy^2 + 1/hz^2): centre weight of the k >= 2 pairs
-    float cx[kMaxR], cy[kMaxR], cz[kMaxR];  // a_k / h^2 per axis
+    float2 c0;              // (a_0 + 2 a_1) (1/hx^2 + 1/hy^2 + 1/hz^2), twice: centre weight of the k >= 2 pairs
+    float2 cx[kMaxR], cy[kMaxR], cz[kMaxR];  // a_k / h^2 per axis, each twice (operands of packed pair ops)
     int n0;                 // time level n at the start of the pass
     // sources: per z-quad column CSR of {x, lane, source, weight bits}, sorted by x
     const int* src_ptr;
@@ -49,7 +49,7 @@ struct PassArgs {
 // blocks of `ry` rows by `qz` z quads, its shared memory and its launcher.
 struct PassShape {
     int R, T, qz, ry;
-    int unroll;  // x-queue rotation: 0 = register moves, 1 = loop unrolled over the queue length
+    int unroll;  // x-queue storage: 0 = registers (moved), 1 = registers (loop unrolled), 2 = tensor memory
     size_t smem;
     cudaError_t (*launch)(const CUtensorMap& mapA, const CUtensorMap& mapV, const CUtensorMap& mapK,
                           const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st);

@@ -1,12 +1,12 @@
 // wave_pass_r8.cu -- instantiations of the pass kernel for stencil radius 8 (SO 16).
-// Each entry is one (T, z quads per row, thread rows, queue rotation) variant the
-// autotuner can pick.
+// Each entry is one (T, z quads per row, thread rows, queue storage) variant the
+// autotuner can pick; queue storage 0/1 = registers (moved / rotated), 2 = tensor memory.
 #include "wave_pass.cuh"
 
 namespace wave {
 
-#define WAVE_SHAPE(T, QZ, RY, ROT) \
-    {8, T, QZ, RY, ROT, detail::smem_bytes<8, T, QZ, RY>(), &detail::launch_impl<8, T, QZ, RY, ROT != 0>}
+#define WAVE_SHAPE(T, QZ, RY, QM) \
+    {8, T, QZ, RY, QM, detail::smem_bytes<8, T, QZ, RY>(), &detail::launch_impl<8, T, QZ, RY, QM>}
 
 const PassShape* pass_shapes_r8(int* n)
 {
@@ -14,8 +14,11 @@ const PassShape* pass_shapes_r8(int* n)
         WAVE_SHAPE(1, 16, 16, 0),
         WAVE_SHAPE(1, 8, 32, 0),
         WAVE_SHAPE(1, 16, 16, 1),
+        WAVE_SHAPE(1, 16, 8, 2),
+        WAVE_SHAPE(1, 16, 16, 2),
         WAVE_SHAPE(2, 8, 32, 0),
         WAVE_SHAPE(2, 8, 32, 1),
+        WAVE_SHAPE(2, 8, 32, 2),
     };
     *n = static_cast<int>(sizeof(shapes) / sizeof(shapes[0]));
     return shapes;
