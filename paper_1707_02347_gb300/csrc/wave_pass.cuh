@@ -169,13 +169,15 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, const float4& v)
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                  "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
-                 "r"(__float_as_uint(v.w))
-                 : "memory");
+                 "r"(__float_as_uint(v.w)));
 }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
 // tmem_ld_xN starts a load of N consecutive columns of the thread's lane into
 // r; tmem_wait_ld(r) waits for every load the thread has started and makes r
 // usable (the registers are its operands, so no use of r can move above it).
+// The tcgen05 loads, stores and waits touch no memory the compiler sees: they
+// carry no memory clobber, so shared-memory loads and stores may be scheduled
+// across them; their order among themselves is kept (asm volatile).
 __device__ __forceinline__ void tmem_ld_x4(uint32_t taddr, uint32_t (&r)[4])
 {
     asm volatile(
@@ -189,9 +191,7 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[4])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  :
-                   "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3])
-                 :
-                 : "memory");
+                   "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
 }
 __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16])
 {
@@ -209,9 +209,7 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16])
                  :
                    "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
                    "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
-                   "+r"(r[14]), "+r"(r[15])
-                 :
-                 : "memory");
+                   "+r"(r[14]), "+r"(r[15]));
 }
 __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32])
 {
@@ -235,9 +233,7 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32])
                    "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
                    "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]),
                    "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]),
-                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
+                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
 }
 __device__ __forceinline__ void tmem_ld_x64(uint32_t taddr, uint32_t (&r)[64])
 {
@@ -272,9 +268,7 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[64])
                    "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]),
                    "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]),
                    "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]),
-                   "+r"(r[63])
-                 :
-                 : "memory");
+                   "+r"(r[63]));
 }
 
 
@@ -501,10 +495,11 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     volatile int* s_abort = reinterpret_cast<volatile int*>(smem + 8 * (NA + NB));
     volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + 8 * (NA + NB) + 4);
-    float* ringA = reinterpret_cast<float*>(smem + hdr);
-    float* ringB = ringA + NA * afl;
-    float* planes = ringB + NB * 2 * bfl;
-    float4* vring = reinterpret_cast<float4*>(planes + 2 * (T - 1) * afl);
+    // disjoint regions: the TMA rings, the published planes, the increment ring
+    float* __restrict__ ringA = reinterpret_cast<float*>(smem + hdr);
+    float* __restrict__ ringB = ringA + NA * afl;
+    float* __restrict__ planes = ringB + NB * 2 * bfl;
+    float4* __restrict__ vring = reinterpret_cast<float4*>(planes + 2 * (T - 1) * afl);
     constexpr uint32_t txA = static_cast<uint32_t>(G::A_ROWS * G::A_COLS * 4);
     constexpr uint32_t txB = static_cast<uint32_t>(2 * G::B_ROWS * G::B_COLS * 4);
 
