@@ -222,9 +222,26 @@ wave_status wave_batch_create(wave_batch_t* out, int nplans, const wave_plan_t* 
  * wave_forward per plan (bit-identical).  rec_out: host array of nplans
  * device pointers ([nt_i][nrec_i] each; may be NULL for shots without
  * receivers).  The graph is captured on the first call and again when the
- * rec_out pointers change.  Synchronises `stream` (cudaStream_t) and
- * reports device-side timeouts. */
+ * rec_out pointers change or a plan's buffers or tiling changed since.
+ * Synchronises `stream` (cudaStream_t) and reports device-side timeouts. */
 wave_status wave_batch_forward(wave_batch_t batch, float* const* rec_out, void* stream);
+
+/* FWI gradient of every shot (see wave_gradient), all shots' work --
+ * checkpointed forward, residual, adjoint sweep, imaging -- captured in one
+ * CUDA graph (one stream per shot) and replayed with a single launch; the
+ * same results as wave_gradient per plan (bit-identical).
+ *   d_obs          : host array of nplans device pointers, [nt_i][nrec_i];
+ *   grad_m         : host array of nplans device pointers, [nx][ny][nz] each
+ *                    (written);
+ *   misfit         : host array of nplans doubles (written), or NULL;
+ *   checkpoint_every: as in wave_gradient, for every shot.
+ * Every buffer a shot needs is allocated before the capture; the graph is
+ * captured again when the pointers, the segment lengths or a plan's buffers
+ * change.  Synchronises `stream`.  Errors: WAVE_ERR_ARG (NULL entries),
+ * WAVE_ERR_STATE (a shot without sources or receivers), WAVE_ERR_OOM,
+ * WAVE_ERR_TIMEOUT, WAVE_ERR_CUDA. */
+wave_status wave_batch_gradient(wave_batch_t batch, const float* const* d_obs, float* const* grad_m, double* misfit,
+                                int checkpoint_every, void* stream);
 
 wave_status wave_batch_destroy(wave_batch_t batch);
 

@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
             "wave_skewed_order_legal": (ctypes.c_int, [ctypes.c_int] * 6),
             "wave_batch_create": (st, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]),
             "wave_batch_forward": (st, [_VP, ctypes.POINTER(_VP), _VP]),
+            "wave_batch_gradient": (st, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _DP, ctypes.c_int, _VP]),
             "wave_batch_destroy": (st, [_VP]),
             "wave_selftest_timeout": (st, [ctypes.c_double]),
             "wave_profile_enable": (st, [_VP, ctypes.c_int]),
@@ -303,7 +304,8 @@ class WavePlan:
 
 class WaveBatch:
     """Several plans (shots) advanced together: one CUDA graph holding every
-    shot's time loop, one stream per shot, one graph launch per call."""
+    shot's time loop (forward) or whole gradient, one stream per shot, one
+    graph launch per call."""
 
     def __init__(self, plans):
         self._lib = load()
@@ -322,6 +324,27 @@ class WaveBatch:
         ptrs = (_VP * len(self.plans))(*[None if r is None else r.data_ptr() for r in recs])
         _check(self._lib.wave_batch_forward(self._h, ptrs, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
         return recs
+
+    def gradient(self, d_obs, checkpoint_every=0, grads=None):
+        """FWI gradient of every shot in one graph launch.  d_obs: one CUDA
+        tensor [nt, nrec] per plan; returns (misfits, grads), grads one CUDA
+        tensor of the grid shape per plan (allocated if None)."""
+        torch = _torch()
+        n = len(self.plans)
+        if len(d_obs) != n:
+            raise ValueError("one d_obs per plan")
+        for p, d in zip(self.plans, d_obs):
+            _dev_ptr(d, "d_obs")
+            if tuple(d.shape) != (p.nt, p.nrec):
+                raise ValueError("d_obs shape %s, expected %s" % (tuple(d.shape), (p.nt, p.nrec)))
+        if grads is None:
+            grads = [torch.empty(p.shape, dtype=torch.float32, device=p.device) for p in self.plans]
+        obs = (_VP * n)(*[d.data_ptr() for d in d_obs])
+        gp = (_VP * n)(*[_dev_ptr(g, "grad") for g in grads])
+        mis = (ctypes.c_double * n)()
+        _check(self._lib.wave_batch_gradient(self._h, obs, gp, mis, int(checkpoint_every),
+                                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return list(mis), grads
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -147,6 +147,9 @@ struct wave_plan_s {
     size_t ev_used = 0;
     double prof_points = 0.0;
     long long launches = 0;
+    // bumped whenever a device buffer or launch parameter that a captured
+    // graph holds is replaced (batched shots recapture when it changes)
+    unsigned long long gen = 0;
 };
 
 namespace {
@@ -333,6 +336,7 @@ wave_status finish(wave_plan_t p)
 wave_status build_taps(wave_plan_t p, TapSet* t, int nsrc, const double* sxyz, int nrec, const double* rxyz)
 {
     t->release();
+    p->gen++;
     ColumnCsr sc, rc;
     std::vector<int> tptr;
     std::vector<float> tw;
@@ -356,6 +360,7 @@ wave_status ensure_slots(wave_plan_t p, size_t floats)
     cudaFree(p->slots);
     p->slots = nullptr;
     p->slots_floats = 0;
+    p->gen++;
     CK(cudaMalloc(&p->slots, floats * 4));
     p->slots_floats = floats;
     return WAVE_OK;
@@ -367,6 +372,7 @@ wave_status ensure_work(wave_plan_t p, size_t bytes)
     cudaFree(p->work);
     p->work = nullptr;
     p->work_bytes = 0;
+    p->gen++;
     CK(cudaMalloc(&p->work, bytes));
     p->work_bytes = bytes;
     return WAVE_OK;
@@ -379,6 +385,7 @@ wave_status apply_tiling(wave_plan_t p, const wave_tiling& t)
     if (!make_geom(p->n, p->R, t, &g, &why)) return fail(WAVE_ERR_ARG, "tiling rejected: " + why);
     p->tiling = t;
     p->geom = g;
+    p->gen++;
     return WAVE_OK;
 }
 
@@ -635,6 +642,7 @@ extern "C" wave_status wave_set_sources(wave_plan_t p, int nsrc, const double* x
     p->adj_ready = false;
     cudaFree(p->wavelet);
     p->wavelet = nullptr;
+    p->gen++;
     if (nsrc > 0 && p->nt > 0) {
         const size_t bytes = static_cast<size_t>(p->nt) * nsrc * 4;
         CK(cudaMalloc(&p->wavelet, bytes));
@@ -742,7 +750,10 @@ extern "C" wave_status wave_forward_host(wave_plan_t p, const float* m_host, con
     wave_status s = set_model_impl(p, p->stage_m);
     if (s) return s;
     if (nsrc > 0 && p->nt > 0) {
-        if (!p->wavelet) CK(cudaMalloc(&p->wavelet, static_cast<size_t>(p->nt) * nsrc * 4));
+        if (!p->wavelet) {
+            CK(cudaMalloc(&p->wavelet, static_cast<size_t>(p->nt) * nsrc * 4));
+            p->gen++;
+        }
         CK(cudaMemcpyAsync(p->wavelet, wavelet_host, static_cast<size_t>(p->nt) * nsrc * 4, cudaMemcpyHostToDevice,
                            p->st));
     }
@@ -788,12 +799,28 @@ extern "C" wave_status wave_adjoint(wave_plan_t p, const float* rec_resid, float
     return finish(p);
 }
 
-extern "C" wave_status wave_gradient(wave_plan_t p, const float* d_obs, float* grad_m, double* misfit,
-                                     int checkpoint_every)
+namespace {
+
+// One gradient evaluation: segment length K and segment count.  Everything
+// it needs on the device is allocated by gradient_prepare, so that
+// gradient_enqueue only issues stream work (and can be captured in a graph).
+struct GradPlan {
+    int K = 0, nseg = 0;
+};
+
+size_t grad_rbytes(wave_plan_t p) { return static_cast<size_t>(p->nt) * p->fwd.nrec * 4; }
+float* grad_rrev(wave_plan_t p)
 {
-    if (!p || !d_obs || !grad_m) return fail(WAVE_ERR_ARG, "wave_gradient: null argument");
+    return reinterpret_cast<float*>(reinterpret_cast<char*>(p->work) + ((grad_rbytes(p) + 255) & ~size_t(255)));
+}
+double* grad_partial(wave_plan_t p)
+{
+    return reinterpret_cast<double*>(reinterpret_cast<char*>(grad_rrev(p)) + ((grad_rbytes(p) + 255) & ~size_t(255)));
+}
+
+wave_status gradient_prepare(wave_plan_t p, int checkpoint_every, GradPlan* gp)
+{
     if (checkpoint_every < 0) return fail(WAVE_ERR_ARG, "wave_gradient: checkpoint_every must be >= 0");
-    DeviceGuard g(p->dev);
     const int nt = p->nt;
     const int nsrc = p->fwd.nsrc, nrec = p->fwd.nrec;
     if (nsrc == 0 || nrec == 0 || !p->wavelet) return fail(WAVE_ERR_STATE, "wave_gradient: needs sources and receivers");
@@ -813,20 +840,34 @@ extern "C" wave_status wave_gradient(wave_plan_t p, const float* d_obs, float* g
         float* l = nullptr;
         CK(cudaMalloc(&l, p->npad * 4));
         p->levels.push_back(l);
+        p->gen++;
     }
+    s = ensure_work(p, 2 * grad_rbytes(p) + 256 * 8 + 1024);
+    if (s) return s;
+    s = ensure_slots(p, static_cast<size_t>(nt) * std::max(p->fwd.ntaps, p->adj.ntaps));
+    if (s) return s;
+    gp->K = K;
+    gp->nseg = nseg;
+    return WAVE_OK;
+}
+
+// Stream work of the gradient on p->st: forward with a checkpoint at the
+// start of every segment, residual and misfit partial sums, then the adjoint
+// sweep segment by segment (recompute the increments of the segment from its
+// checkpoint, then step the adjoint back through it, imaging as it goes).
+wave_status gradient_enqueue(wave_plan_t p, const GradPlan& gp, const float* d_obs, float* grad_m)
+{
+    const int nt = p->nt, K = gp.K, nseg = gp.nseg;
+    const int nrec = p->fwd.nrec;
     float** ck = p->levels.data();                  // [2 nseg]: (u^{cK}, v^{cK-1/2})
     float** seg = p->levels.data() + 2 * nseg;      // [K + 1]: v^{t0-1/2} .. v^{t0+K-1/2}
     float* uspare = p->levels[2 * nseg + K + 1];    // second u buffer of the recompute
-    const size_t rbytes = static_cast<size_t>(nt) * nrec * 4;
-    s = ensure_work(p, 2 * rbytes + 256 * 8 + 1024);
-    if (s) return s;
     float* rec = p->work;
-    float* rrev = reinterpret_cast<float*>(reinterpret_cast<char*>(p->work) + ((rbytes + 255) & ~size_t(255)));
-    double* partial = reinterpret_cast<double*>(reinterpret_cast<char*>(rrev) + ((rbytes + 255) & ~size_t(255)));
+    float* rrev = grad_rrev(p);
+    double* partial = grad_partial(p);
+    wave_status s = WAVE_OK;
     CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
     // 1) forward, keeping a checkpoint at the start of every segment
-    s = ensure_slots(p, static_cast<size_t>(nt) * std::max(p->fwd.ntaps, p->adj.ntaps));
-    if (s) return s;
     Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
     CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
     CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
@@ -840,11 +881,9 @@ extern "C" wave_status wave_gradient(wave_plan_t p, const float* d_obs, float* g
     if (p->fwd.ntaps > 0)
         CKL(launch_rec_reduce(p->slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec, nt, nrec, p->fwd.ntaps, p->st));
     else
-        CK(cudaMemsetAsync(rec, 0, rbytes, p->st));
-    // 2) residual (time-reversed) and misfit
+        CK(cudaMemsetAsync(rec, 0, grad_rbytes(p), p->st));
+    // 2) residual (time-reversed) and misfit partial sums
     CKL(launch_residual(rec, d_obs, rrev, partial, nt, nrec, p->st));
-    std::vector<double> hp(256);
-    CK(cudaMemcpyAsync(hp.data(), partial, 256 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
     // 3) adjoint sweep, segment by segment (the adjoint runs the same update backwards)
     Fields a{p->buf[2], p->buf[3], p->buf[1], nullptr};  // (mu, its increment), spare
     CK(cudaMemsetAsync(a.u, 0, p->npad * 4, p->st));
@@ -875,14 +914,35 @@ extern "C" wave_status wave_gradient(wave_plan_t p, const float* d_obs, float* g
         }
     }
     CKL(launch_unpad_grad(gacc, grad_m, p->n[0], p->n[1], p->n[2], p->nzp, p->st));
+    return WAVE_OK;
+}
+
+// Misfit 1/2 sum (rec - d_obs)^2 from the partial sums, once the stream is done.
+wave_status gradient_misfit(wave_plan_t p, double* misfit)
+{
+    double hp[256];
+    CK(cudaMemcpy(hp, grad_partial(p), sizeof(hp), cudaMemcpyDeviceToHost));
+    double J = 0.0;
+    for (double v : hp) J += v;
+    *misfit = 0.5 * J;
+    return WAVE_OK;
+}
+
+}  // namespace
+
+extern "C" wave_status wave_gradient(wave_plan_t p, const float* d_obs, float* grad_m, double* misfit,
+                                     int checkpoint_every)
+{
+    if (!p || !d_obs || !grad_m) return fail(WAVE_ERR_ARG, "wave_gradient: null argument");
+    DeviceGuard g(p->dev);
+    GradPlan gp;
+    wave_status s = gradient_prepare(p, checkpoint_every, &gp);
+    if (s) return s;
+    s = gradient_enqueue(p, gp, d_obs, grad_m);
+    if (s) return s;
     s = finish(p);
     if (s) return s;
-    if (misfit) {
-        double J = 0.0;
-        for (double v : hp) J += v;
-        *misfit = 0.5 * J;
-    }
-    return WAVE_OK;
+    return misfit ? gradient_misfit(p, misfit) : WAVE_OK;
 }
 
 extern "C" wave_status wave_profile_enable(wave_plan_t p, int enable)
@@ -926,11 +986,20 @@ struct wave_batch_s {
     std::vector<wave_plan_t> plans;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
-    std::vector<float*> recs;  // rec_out pointers the graph was captured with
     cudaStream_t cap = nullptr;
+    int dev = 0;
+    // forward graph and what it was captured with
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int dev = 0;
+    std::vector<float*> recs;
+    std::vector<unsigned long long> gens;
+    // gradient graph and what it was captured with
+    cudaGraph_t ggraph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const float*> gobs;
+    std::vector<float*> ggrad;
+    std::vector<int> gK;
+    std::vector<unsigned long long> ggens;
 };
 
 namespace {
@@ -941,6 +1010,70 @@ void batch_release_graph(wave_batch_t b)
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
+}
+
+void batch_release_ggraph(wave_batch_t b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->ggraph) cudaGraphDestroy(b->ggraph);
+    b->gexec = nullptr;
+    b->ggraph = nullptr;
+}
+
+std::vector<unsigned long long> batch_gens(wave_batch_t b)
+{
+    std::vector<unsigned long long> g;
+    for (auto* p : b->plans) g.push_back(p->gen);
+    return g;
+}
+
+// Capture enqueue(i) for every shot i, shot i on streams[i] (forked from and
+// joined back into the capture stream), into *graph / *exec.
+template <class F>
+wave_status batch_capture_with(wave_batch_t b, cudaGraph_t* graph, cudaGraphExec_t* exec, F enqueue)
+{
+    const size_t n = b->plans.size();
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    wave_status st = WAVE_OK;
+    cudaError_t e = cudaEventRecord(b->events[n], b->cap);
+    if (e != cudaSuccess) st = check_cuda("cudaEventRecord", e);
+    for (size_t i = 0; i < n && !st; ++i) {
+        wave_plan_t p = b->plans[i];
+        cudaStream_t keep = p->st;
+        p->st = b->streams[i];
+        e = cudaStreamWaitEvent(p->st, b->events[n], 0);
+        if (e != cudaSuccess) st = check_cuda("cudaStreamWaitEvent", e);
+        if (!st) st = enqueue(i);
+        if (!st) {
+            e = cudaEventRecord(b->events[i], p->st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->events[i], 0);
+            if (e != cudaSuccess) st = check_cuda("event join", e);
+        }
+        p->st = keep;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return check_cuda("cudaStreamEndCapture", e);
+    *graph = g;
+    CK(cudaGraphInstantiate(exec, g, 0));
+    return WAVE_OK;
+}
+
+// Launch a captured graph, wait, and check every shot's error word.
+wave_status batch_run(wave_batch_t b, cudaGraphExec_t exec, cudaStream_t st)
+{
+    for (auto* p : b->plans) CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+    CK(cudaGraphLaunch(exec, st));
+    CK(cudaStreamSynchronize(st));
+    for (auto* p : b->plans) {
+        CK(cudaMemcpy(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (*p->err_host) return fail(WAVE_ERR_TIMEOUT, "a bounded device-side wait gave up in a batched shot");
+    }
+    return WAVE_OK;
 }
 
 // Capture forward_impl of every plan; plan i runs on streams[i].
@@ -959,33 +1092,12 @@ wave_status batch_capture(wave_batch_t b, float* const* rec_out)
         }
     }
     batch_release_graph(b);
-    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    wave_status st = WAVE_OK;
-    CK(cudaEventRecord(b->events[n], b->cap));
-    for (size_t i = 0; i < n && !st; ++i) {
-        wave_plan_t p = b->plans[i];
-        cudaStream_t keep = p->st;
-        p->st = b->streams[i];
-        cudaError_t e = cudaStreamWaitEvent(p->st, b->events[n], 0);
-        if (e != cudaSuccess) st = check_cuda("cudaStreamWaitEvent", e);
-        if (!st) st = forward_impl(p, nullptr, rec_out ? rec_out[i] : nullptr, nullptr);
-        if (!st) {
-            e = cudaEventRecord(b->events[i], p->st);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->events[i], 0);
-            if (e != cudaSuccess) st = check_cuda("event join", e);
-        }
-        p->st = keep;
-    }
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
-    if (st) {
-        if (g) cudaGraphDestroy(g);
-        return st;
-    }
-    if (e != cudaSuccess) return check_cuda("cudaStreamEndCapture", e);
-    b->graph = g;
-    CK(cudaGraphInstantiate(&b->exec, g, 0));
+    wave_status s = batch_capture_with(b, &b->graph, &b->exec, [&](size_t i) {
+        return forward_impl(b->plans[i], nullptr, rec_out ? rec_out[i] : nullptr, nullptr);
+    });
+    if (s) return s;
     b->recs.assign(rec_out ? rec_out : nullptr, rec_out ? rec_out + n : nullptr);
+    b->gens = batch_gens(b);
     return WAVE_OK;
 }
 
@@ -1028,19 +1140,49 @@ extern "C" wave_status wave_batch_forward(wave_batch_t b, float* const* rec_out,
     if (!b) return fail(WAVE_ERR_ARG, "wave_batch_forward: null batch");
     DeviceGuard g(b->dev);
     const size_t n = b->plans.size();
-    bool same = b->exec && b->recs.size() == (rec_out ? n : 0);
+    bool same = b->exec && b->recs.size() == (rec_out ? n : 0) && b->gens == batch_gens(b);
     for (size_t i = 0; same && rec_out && i < n; ++i) same = b->recs[i] == rec_out[i];
     if (!same) {
         wave_status s = batch_capture(b, rec_out);
         if (s) return s;
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (auto* p : b->plans) CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
-    CK(cudaGraphLaunch(b->exec, st));
-    CK(cudaStreamSynchronize(st));
-    for (auto* p : b->plans) {
-        CK(cudaMemcpy(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (*p->err_host) return fail(WAVE_ERR_TIMEOUT, "a bounded device-side wait gave up in a batched shot");
+    return batch_run(b, b->exec, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" wave_status wave_batch_gradient(wave_batch_t b, const float* const* d_obs, float* const* grad_m,
+                                           double* misfit, int checkpoint_every, void* stream)
+{
+    if (!b || !d_obs || !grad_m) return fail(WAVE_ERR_ARG, "wave_batch_gradient: null argument");
+    const size_t n = b->plans.size();
+    for (size_t i = 0; i < n; ++i)
+        if (!d_obs[i] || !grad_m[i]) return fail(WAVE_ERR_ARG, "wave_batch_gradient: null d_obs or grad_m entry");
+    DeviceGuard g(b->dev);
+    // allocate everything every shot's gradient needs (may replace buffers)
+    std::vector<GradPlan> gps(n);
+    std::vector<int> K(n);
+    for (size_t i = 0; i < n; ++i) {
+        wave_status s = gradient_prepare(b->plans[i], checkpoint_every, &gps[i]);
+        if (s) return s;
+        K[i] = gps[i].K;
+    }
+    bool same = b->gexec && b->gK == K && b->ggens == batch_gens(b);
+    for (size_t i = 0; same && i < n; ++i) same = b->gobs[i] == d_obs[i] && b->ggrad[i] == grad_m[i];
+    if (!same) {
+        batch_release_ggraph(b);
+        wave_status s = batch_capture_with(b, &b->ggraph, &b->gexec, [&](size_t i) {
+            return gradient_enqueue(b->plans[i], gps[i], d_obs[i], grad_m[i]);
+        });
+        if (s) return s;
+        b->gobs.assign(d_obs, d_obs + n);
+        b->ggrad.assign(grad_m, grad_m + n);
+        b->gK = K;
+        b->ggens = batch_gens(b);
+    }
+    wave_status s = batch_run(b, b->gexec, static_cast<cudaStream_t>(stream));
+    if (s) return s;
+    for (size_t i = 0; misfit && i < n; ++i) {
+        s = gradient_misfit(b->plans[i], &misfit[i]);
+        if (s) return s;
     }
     return WAVE_OK;
 }
@@ -1051,6 +1193,7 @@ extern "C" wave_status wave_batch_destroy(wave_batch_t b)
     DeviceGuard g(b->dev);
     if (b->cap) cudaStreamSynchronize(b->cap);
     batch_release_graph(b);
+    batch_release_ggraph(b);
     for (auto s : b->streams) cudaStreamDestroy(s);
     for (auto e : b->events) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
