@@ -9,6 +9,7 @@
 // source or receiver is binned into the CSR list of its z-quad column, sorted
 // by x, so the thread that owns the column meets it while it streams along x.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -117,6 +118,38 @@ void build_receiver_csr(int nrec, const double* xyz, const double h[3], const in
         out->ent[2 * i + 1] = (e[i].tap << 2) | e[i].lane;
     }
     for (int c = 0; c < ncols; ++c) out->ptr[c + 1] += out->ptr[c];
+}
+
+// Capture plan of a dense receiver surface: when every tap of every receiver
+// lies in at most two adjacent z quads, the pass kernel can store those quads
+// whole (coalesced) and the traces are gathered afterwards.  idx[t] is the
+// float offset of tap t (receiver order, as tw) within one step's capture
+// slice [nx][ny][nq][4].  False (no plan) for fewer than min_rec receivers,
+// taps in more than two quads, or a slice over 2^31 floats.
+bool receiver_capture_plan(int nrec, const double* xyz, const double h[3], const int n[3], int min_rec, int* q0,
+                           int* nq, std::vector<int>* idx)
+{
+    if (nrec < min_rec) return false;
+    int qlo = INT_MAX, qhi = -1;
+    std::vector<Tap> all;
+    for (int r = 0; r < nrec; ++r) {
+        Tap t[8];
+        const int c = trilinear_taps(xyz + 3 * r, h, n, t);
+        for (int j = 0; j < c; ++j) {
+            all.push_back(t[j]);
+            qlo = std::min(qlo, t[j].k / 4);
+            qhi = std::max(qhi, t[j].k / 4);
+        }
+    }
+    if (all.empty() || qhi - qlo > 1) return false;
+    const int q = qhi - qlo + 1;
+    if (static_cast<long long>(n[0]) * n[1] * q * 4 > 0x7fffffffLL) return false;
+    idx->resize(all.size());
+    for (size_t t = 0; t < all.size(); ++t)
+        (*idx)[t] = ((all[t].i * n[1] + all[t].j) * q + (all[t].k / 4 - qlo)) * 4 + all[t].k % 4;
+    *q0 = qlo;
+    *nq = q;
+    return true;
 }
 
 // Sponge (the paper's `damp` array, whose profile it does not give): for a

@@ -64,9 +64,15 @@ struct TapSet {
     int2* rec_ent = nullptr;
     int* rec_tptr = nullptr;
     float* rec_tw = nullptr;
+    // capture mode (dense receiver surface): per tap its offset in a step's
+    // capture slice; nullptr = receivers are recorded through the CSR
+    int* cap_idx = nullptr;
+    int cap_q0 = 0, cap_nq = 0;
+    long long cap_slice = 0;
     void release()
     {
         cudaFree(src_ptr); cudaFree(src_ent); cudaFree(rec_ptr); cudaFree(rec_ent); cudaFree(rec_tptr); cudaFree(rec_tw);
+        cudaFree(cap_idx);
         *this = TapSet();
     }
 };
@@ -125,6 +131,8 @@ struct wave_plan_s {
     bool adj_ready = false;
     float* slots = nullptr;
     size_t slots_floats = 0;
+    float* capbuf = nullptr;  // capture slices of one pass (capture mode)
+    size_t cap_floats = 0;
     // coefficients
     float c0 = 0.f, cx[kMaxR] = {}, cy[kMaxR] = {}, cz[kMaxR] = {};
     // tiling
@@ -257,6 +265,16 @@ wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const
     a.n0 = n0;
     a.out_u = out_u;
     a.out_v = out_v;
+    // capture mode: slots is the trace array [nt][nrec]; the kernel stores the
+    // receivers' z quads whole, and the traces of the pass are gathered after it
+    const bool capture = taps.cap_idx && slots && taps.nrec > 0;
+    if (capture) {
+        a.rec_ptr = nullptr;
+        a.cap = p->capbuf;
+        a.cap_slice = taps.cap_slice;
+        a.cap_q0 = taps.cap_q0;
+        a.cap_nq = taps.cap_nq;
+    }
     cudaError_t e = cudaSuccess;
     if (p->prof) {
         if (p->ev_used + 2 > p->ev.size()) {
@@ -271,6 +289,11 @@ wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const
     if (!g.shape) return fail(WAVE_ERR_ARG, "no compiled kernel for this tile shape");
     e = g.shape->launch(*mA, *mV, *mK, a, g.block, g.smem, g.blocks, p->st);
     p->launches++;
+    if (capture && e == cudaSuccess) {
+        e = launch_cap_reduce(p->capbuf, taps.cap_slice, taps.cap_idx, taps.rec_tptr, taps.rec_tw,
+                              slots + static_cast<long long>(n0) * taps.nrec, g.T, taps.nrec, p->st);
+        p->launches++;
+    }
     if (p->prof) {
         CK(cudaEventRecord(p->ev[p->ev_used + 1], p->st));
         p->ev_used += 2;
@@ -333,7 +356,21 @@ wave_status finish(wave_plan_t p)
     return WAVE_OK;
 }
 
-wave_status build_taps(wave_plan_t p, TapSet* t, int nsrc, const double* sxyz, int nrec, const double* rxyz)
+// Receivers at least this many, all in one or two z quads: capture mode.
+constexpr int kCaptureMinReceivers = 4096;
+
+int max_pass_T()
+{
+    int n = 0, T = 1;
+    const PassShape* s = pass_shapes(&n);
+    for (int i = 0; i < n; ++i) T = std::max(T, s[i].T);
+    return T;
+}
+
+// Taps of the sources and receivers of one direction (the adjoint swaps
+// them); allow_capture lets a dense receiver surface use capture mode.
+wave_status build_taps(wave_plan_t p, TapSet* t, int nsrc, const double* sxyz, int nrec, const double* rxyz,
+                       bool allow_capture)
 {
     t->release();
     p->gen++;
@@ -351,6 +388,22 @@ wave_status build_taps(wave_plan_t p, TapSet* t, int nsrc, const double* sxyz, i
     CK(upload(&t->rec_ent, rc.ent.data(), rc.ent.size() * 4, p->st));
     CK(upload(&t->rec_tptr, tptr.data(), tptr.size() * 4, p->st));
     CK(upload(&t->rec_tw, tw.data(), tw.size() * 4, p->st));
+    std::vector<int> idx;
+    int q0 = 0, nq = 0;
+    if (allow_capture && receiver_capture_plan(nrec, rxyz, p->h, p->n, kCaptureMinReceivers, &q0, &nq, &idx)) {
+        CK(upload(&t->cap_idx, idx.data(), idx.size() * 4, p->st));
+        t->cap_q0 = q0;
+        t->cap_nq = nq;
+        t->cap_slice = static_cast<long long>(p->n[0]) * p->n[1] * nq * 4;
+        const size_t need = static_cast<size_t>(t->cap_slice) * max_pass_T();
+        if (need > p->cap_floats) {
+            cudaFree(p->capbuf);
+            p->capbuf = nullptr;
+            p->cap_floats = 0;
+            CK(cudaMalloc(&p->capbuf, need * 4));
+            p->cap_floats = need;
+        }
+    }
     return WAVE_OK;
 }
 
@@ -463,6 +516,7 @@ void destroy(wave_plan_t p)
     cudaFree(p->stage_r);
     for (auto* l : p->levels) cudaFree(l);
     cudaFree(p->work);
+    cudaFree(p->capbuf);
     for (auto e : p->ev) cudaEventDestroy(e);
     delete p;
 }
@@ -479,15 +533,20 @@ wave_status forward_impl(wave_plan_t p, const float* u_init, float* rec_out, flo
         CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
         CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
     }
+    // receivers: tap values into slots, reduced at the end; in capture mode
+    // the traces are gathered into rec_out after every pass
+    const bool capture = p->fwd.cap_idx && p->fwd.nrec > 0 && p->nt > 0;
     float* slots = nullptr;
-    if (p->fwd.nrec > 0 && p->fwd.ntaps > 0) {
+    if (capture) {
+        slots = rec_out;
+    } else if (p->fwd.nrec > 0 && p->fwd.ntaps > 0) {
         wave_status s = ensure_slots(p, static_cast<size_t>(p->nt) * p->fwd.ntaps);
         if (s) return s;
         slots = p->slots;
     }
     wave_status s = advance(p, &f, p->fwd, p->wavelet, slots, 0, p->nt, true);
     if (s) return s;
-    if (p->fwd.nrec > 0 && p->nt > 0) {
+    if (p->fwd.nrec > 0 && p->nt > 0 && !capture) {
         if (p->fwd.ntaps > 0)
             CKL(launch_rec_reduce(slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec_out, p->nt, p->fwd.nrec, p->fwd.ntaps,
                                  p->st));
@@ -502,7 +561,7 @@ wave_status ensure_adjoint_taps(wave_plan_t p)
 {
     if (p->adj_ready) return WAVE_OK;
     const int nsrc = static_cast<int>(p->src_xyz.size() / 3), nrec = static_cast<int>(p->rec_xyz.size() / 3);
-    wave_status s = build_taps(p, &p->adj, nrec, p->rec_xyz.data(), nsrc, p->src_xyz.data());
+    wave_status s = build_taps(p, &p->adj, nrec, p->rec_xyz.data(), nsrc, p->src_xyz.data(), false);
     if (s) return s;
     p->adj_ready = true;
     return WAVE_OK;
@@ -649,7 +708,7 @@ extern "C" wave_status wave_set_sources(wave_plan_t p, int nsrc, const double* x
         CK(cudaMemcpyAsync(p->wavelet, wavelet, bytes, cudaMemcpyDefault, p->st));
     }
     const int nrec = static_cast<int>(p->rec_xyz.size() / 3);
-    return build_taps(p, &p->fwd, nsrc, p->src_xyz.data(), nrec, p->rec_xyz.data());
+    return build_taps(p, &p->fwd, nsrc, p->src_xyz.data(), nrec, p->rec_xyz.data(), true);
 }
 
 extern "C" wave_status wave_set_receivers(wave_plan_t p, int nrec, const double* xyz)
@@ -660,7 +719,7 @@ extern "C" wave_status wave_set_receivers(wave_plan_t p, int nrec, const double*
     p->rec_xyz.assign(xyz, xyz + 3 * static_cast<size_t>(nrec));
     p->adj_ready = false;
     const int nsrc = static_cast<int>(p->src_xyz.size() / 3);
-    return build_taps(p, &p->fwd, nsrc, p->src_xyz.data(), nrec, p->rec_xyz.data());
+    return build_taps(p, &p->fwd, nsrc, p->src_xyz.data(), nrec, p->rec_xyz.data(), true);
 }
 
 extern "C" wave_status wave_set_tiling(wave_plan_t p, const wave_tiling* t)
@@ -871,17 +930,20 @@ wave_status gradient_enqueue(wave_plan_t p, const GradPlan& gp, const float* d_o
     Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
     CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
     CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
+    const bool capture = p->fwd.cap_idx != nullptr;  // traces gathered into rec after every pass
     for (int c = 0; c < nseg; ++c) {
         CK(cudaMemcpyAsync(ck[2 * c], f.u, p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
         CK(cudaMemcpyAsync(ck[2 * c + 1], f.v, p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
         const int steps = std::min(K, nt - c * K);
-        s = advance(p, &f, p->fwd, p->wavelet, p->slots, c * K, steps, true);
+        s = advance(p, &f, p->fwd, p->wavelet, capture ? rec : p->slots, c * K, steps, true);
         if (s) return s;
     }
-    if (p->fwd.ntaps > 0)
-        CKL(launch_rec_reduce(p->slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec, nt, nrec, p->fwd.ntaps, p->st));
-    else
-        CK(cudaMemsetAsync(rec, 0, grad_rbytes(p), p->st));
+    if (!capture) {
+        if (p->fwd.ntaps > 0)
+            CKL(launch_rec_reduce(p->slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec, nt, nrec, p->fwd.ntaps, p->st));
+        else
+            CK(cudaMemsetAsync(rec, 0, grad_rbytes(p), p->st));
+    }
     // 2) residual (time-reversed) and misfit partial sums
     CKL(launch_residual(rec, d_obs, rrev, partial, nt, nrec, p->st));
     // 3) adjoint sweep, segment by segment (the adjoint runs the same update backwards)
@@ -1086,7 +1148,7 @@ wave_status batch_capture(wave_batch_t b, float* const* rec_out)
         if (p->fwd.nrec > 0 && p->nt > 0 && (!rec_out || !rec_out[i]))
             return fail(WAVE_ERR_ARG, "wave_batch_forward: a shot with receivers has no rec_out");
         // everything forward_impl would allocate is allocated before the capture
-        if (p->fwd.nrec > 0 && p->fwd.ntaps > 0) {
+        if (p->fwd.nrec > 0 && p->fwd.ntaps > 0 && !p->fwd.cap_idx) {
             wave_status s = ensure_slots(p, static_cast<size_t>(p->nt) * p->fwd.ntaps);
             if (s) return s;
         }

@@ -65,6 +65,23 @@ __global__ void rec_reduce_kernel(const float* __restrict__ slots, const int* __
     }
 }
 
+// Traces of one pass from the captured quads: the taps of each receiver in
+// the order (and with the arithmetic) of rec_reduce_kernel.
+__global__ void cap_reduce_kernel(const float* __restrict__ cap, long long slice, const int* __restrict__ cap_idx,
+                                  const int* __restrict__ tptr, const float* __restrict__ tw, float* __restrict__ rec,
+                                  int T, int nrec)
+{
+    const long long n = static_cast<long long>(T) * nrec;
+    for (long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int j = static_cast<int>(p % nrec);
+        const float* c = cap + (p / nrec) * slice;
+        float acc = 0.f;
+        for (int t = tptr[j]; t < tptr[j + 1]; ++t) acc = __fmaf_rn(tw[t], c[cap_idx[t]], acc);
+        rec[p] = acc;
+    }
+}
+
 // grad -= scale * mu * (v_new - v_old), scale = 1/dt^2: the imaging condition
 // mu^{n+1} (u^{n+1} - 2u^n + u^{n-1}) / dt^2 with u^{n+1} - u^n = v^{n+1/2}.
 __global__ void grad_accum_kernel(float* __restrict__ grad, const float* __restrict__ mu,
@@ -183,6 +200,14 @@ const PassShape* find_pass_shape(int R, int T, int qz, int ry, int unroll)
     for (int i = 0; i < n; ++i)
         if (s[i].R == R && s[i].T == T && s[i].qz == qz && s[i].ry == ry && s[i].unroll == unroll) return &s[i];
     return nullptr;
+}
+
+cudaError_t launch_cap_reduce(const float* cap, long long slice, const int* cap_idx, const int* tptr, const float* tw,
+                              float* rec, int T, int nrec, cudaStream_t st)
+{
+    cap_reduce_kernel<<<grid_for(static_cast<long long>(T) * nrec, 256), 256, 0, st>>>(cap, slice, cap_idx, tptr, tw,
+                                                                                      rec, T, nrec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_kappa(const float* m, float* kap, int nx, int ny, int nz, int nzp, float dt2, cudaStream_t st)

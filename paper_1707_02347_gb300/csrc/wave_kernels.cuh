@@ -42,6 +42,12 @@ struct PassArgs {
     float* slots;           // [rows][ntaps]
     int ntaps;
     int slot_row0;          // rec row stored in slot row 0
+    // dense receiver surfaces (capture mode, receivers not in the CSR): the
+    // output quads of z quads [cap_q0, cap_q0 + cap_nq) are stored whole, step
+    // k of the pass at cap + k * cap_slice + ((x * ny + y) * cap_nq + q) * 4
+    float* cap;
+    long long cap_slice;
+    int cap_q0, cap_nq;
     int* err;               // device error word (bit 0: a bounded wait gave up)
 };
 
@@ -72,6 +78,10 @@ cudaError_t launch_final_state(const float* u, const float* v, float* u2, int nx
                                cudaStream_t st);
 cudaError_t launch_rec_reduce(const float* slots, const int* tptr, const float* tw, float* rec, int rows,
                               int nrec, int ntaps, cudaStream_t st);
+// rec[k][j] = sum over the taps t of receiver j (in order) of tw[t] * cap[k * slice + cap_idx[t]], k < T:
+// the same sums in the same order as launch_rec_reduce, from the captured quads of one pass.
+cudaError_t launch_cap_reduce(const float* cap, long long slice, const int* cap_idx, const int* tptr, const float* tw,
+                              float* rec, int T, int nrec, cudaStream_t st);
 // grad -= scale * mu * (v_new - v_old)   (scale = 1/dt^2)
 cudaError_t launch_grad_accum(float* grad, const float* mu, const float* v_new, const float* v_old, long long n,
                               float scale, cudaStream_t st);

@@ -19,6 +19,7 @@ const PassShape* pass_shapes_r4(int* n)
         WAVE_SHAPE(1, 8, 32, 1),
         WAVE_SHAPE(1, 16, 8, 2),
         WAVE_SHAPE(1, 16, 16, 2),
+        WAVE_SHAPE(1, 16, 32, 2),
         WAVE_SHAPE(2, 16, 24, 0),
         WAVE_SHAPE(2, 8, 32, 0),
         WAVE_SHAPE(2, 16, 16, 0),

@@ -97,9 +97,10 @@ def test_plain_forward_64_so4_vs_oracle(W, oracle):
     (8, (41, 35, 38), [(1, 32, 32, 40), (2, 24, 24, 10), (2, 16, 56, 41), (3, 16, 16, 17), (1, 32, 32, 41, 1),
                        (1, 16, 64, 23, 1), (2, 16, 56, 41, 1), (2, 24, 24, 29, 1), (3, 16, 16, 40, 1),
                        (1, 8, 64, 41, 2), (1, 16, 64, 23, 2), (2, 16, 56, 41, 2), (2, 24, 56, 29, 2),
-                       (2, 56, 24, 17, 2), (3, 16, 16, 40, 2)]),
+                       (2, 56, 24, 17, 2), (3, 16, 16, 40, 2), (1, 32, 64, 41, 2)]),
     (16, (36, 33, 34), [(1, 16, 64, 12), (2, 16, 16, 12), (2, 16, 16, 40), (1, 32, 32, 7), (1, 16, 64, 36, 1),
-                        (2, 16, 16, 36, 1), (1, 8, 64, 36, 2), (1, 16, 64, 12, 2), (2, 16, 16, 36, 2)]),
+                        (2, 16, 16, 36, 1), (1, 8, 64, 36, 2), (1, 16, 64, 12, 2), (2, 16, 16, 36, 2),
+                        (1, 32, 64, 36, 2)]),
 ])
 def test_tiled_bit_identical_to_one_step(W, oracle, so, shape, tilings):
     nt = 23
@@ -217,3 +218,28 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(W, oracle):
     rec_o, _, uc_o = run_oracle(oracle, w)
     rec, uf = run_gpu(W, w, (2, 12, 56, 20))
     assert rel_l2(uf[1], uc_o) <= TOL and rel_l2(rec, rec_o) <= TOL
+
+
+@pytest.mark.parametrize("so", [8, 16])
+def test_dense_receiver_surface_capture_mode(W, oracle, so):
+    """64 x 64 surface receivers at 25 m (all taps in the first z quad): the
+    capture path (quads stored whole, traces gathered per pass) gives the
+    same traces bit for bit as the per-tap path (forced by one extra receiver
+    deeper down), across one-step and tiled passes, and matches the oracle."""
+    from paper_1707_02347_gb300 import inputs
+
+    shape = (40, 37, 30)
+    w = small_layered(shape, so, 21, seed=31, nrec=0)
+    surf = inputs.surface_receivers(shape, w.spacing, 64, 25.0)
+    deep = np.vstack([surf, [[150.0, 160.0, 215.0]]])  # taps in a third z quad: per-tap path
+    tilings = [(1, 16, 64, 40, 2), (2, 16, 56, 40, 2) if so == 8 else (2, 16, 16, 40, 2), (1, 16, 64, 40, 0)]
+    w.rec_xyz = surf
+    cap = [run_gpu(W, w, t)[0] for t in tilings]
+    w.rec_xyz = deep
+    csr = [run_gpu(W, w, t)[0] for t in tilings]
+    for a, b in zip(cap, csr):
+        assert np.array_equal(a, cap[0])
+        assert np.array_equal(b[:, :-1], cap[0])
+    w.rec_xyz = surf
+    rec_o, _, _ = run_oracle(oracle, w)
+    assert rel_l2(cap[0], rec_o) <= TOL

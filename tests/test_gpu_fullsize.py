@@ -1,0 +1,115 @@
+"""Parity at the full 512^3 SO8 size, in the launch configurations the
+benchmark times (T = 1 and T = 2 passes with the x queues in tensor memory).
+
+The FP64 oracle cannot run the whole grid, so outputs are checked one by one:
+the GPU runs the workload for n1 steps and keeps the state (u^{n1-1}, u^{n1});
+then it advances one more pass (T steps) from that state.  For each sampled
+point p the oracle advances the same T steps on a window around p that
+reaches r T points past p on every side (clipped at the grid, where its zero
+ghosts are the grid's), starting from the GPU's state in FP64.  After T steps
+the oracle's value at p depends only on the window, so it is the exact result
+of the paper's update at p.  Sampled points: near the source, at the free
+surface, in the sponge, on the receiver line, and at random.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+N = 512
+SO = 8
+R = SO // 2
+N1 = 110  # steps before the checked pass (the 15 Hz Ricker peaks near step 77)
+
+
+@pytest.fixture(scope="module")
+def state(oracle):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1707_02347_gb300 as W
+    from paper_1707_02347_gb300 import inputs
+
+    W.load()
+    dev = torch.device("cuda")
+    w = inputs.layered_forward((N, N, N), SO, N1 + 2, seed=1, f=15.0, h=10.0, sponge_width=10, nrec_line=512)
+    m = torch.from_numpy(np.ascontiguousarray(w.m)).to(dev)
+    wav = np.ascontiguousarray(w.wavelet.astype(np.float32))
+    plan = W.WavePlan(w.shape, w.spacing, SO, w.dt, N1, m, sponge_width=w.sponge_width, vmax=w.vmax,
+                      tiling=(1, 8, 64, 64, 2))
+    plan.set_sources(w.src_xyz, torch.from_numpy(wav[:N1]).to(dev))
+    plan.set_receivers(w.rec_xyz)
+    _, uA = plan.forward(want_final=True)
+    plan.close()
+    out = {}
+    for T, tiling in ((1, (1, 8, 64, 64, 2)), (2, (2, 24, 56, 128, 2))):
+        p = W.WavePlan(w.shape, w.spacing, SO, w.dt, T, m, sponge_width=w.sponge_width, vmax=w.vmax, tiling=tiling)
+        p.set_sources(w.src_xyz, torch.from_numpy(wav[N1:N1 + T].copy()).to(dev))
+        _, uB = p.forward(u_init=uA, want_final=True)
+        torch.cuda.synchronize()
+        out[T] = uB[1].cpu().numpy()
+        p.close()
+    # two one-step passes from the same state: bit-identical to the T = 2 pass
+    p = W.WavePlan(w.shape, w.spacing, SO, w.dt, 2, m, sponge_width=w.sponge_width, vmax=w.vmax,
+                   tiling=(1, 8, 64, 64, 2))
+    p.set_sources(w.src_xyz, torch.from_numpy(wav[N1:N1 + 2].copy()).to(dev))
+    _, uC = p.forward(u_init=uA, want_final=True)
+    torch.cuda.synchronize()
+    out["T1x2"] = uC[1].cpu().numpy()
+    p.close()
+    A = uA.cpu().numpy()
+    return w, A, out
+
+
+def _samples(w, rng):
+    src = np.round(w.src_xyz[0] / np.asarray(w.spacing)).astype(int)
+    pts = []
+    for _ in range(24):  # around the source, where the wavefield is
+        pts.append(np.clip(src + rng.integers(-14, 15, 3), 0, N - 1))
+    for _ in range(8):  # free surface z = 0 .. 3
+        pts.append(np.array([src[0] + rng.integers(-12, 13), src[1] + rng.integers(-12, 13), rng.integers(0, 4)]))
+    for _ in range(8):  # sponge layers, every face
+        a = rng.integers(0, 3)
+        p = rng.integers(0, N, 3)
+        p[a] = rng.integers(0, 10) if rng.integers(0, 2) else N - 1 - rng.integers(0, 10)
+        pts.append(p)
+    for _ in range(8):  # grid corners and edges
+        pts.append(np.array([rng.choice([0, 1, N - 2, N - 1]) for _ in range(3)]))
+    for _ in range(8):  # anywhere
+        pts.append(rng.integers(0, N, 3))
+    return [tuple(int(c) for c in p) for p in pts]
+
+
+def _oracle_at(oracle, w, A, p, T):
+    lo = [max(0, c - R * T) for c in p]
+    hi = [min(N, c + R * T + 1) for c in p]
+    sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+    shape = tuple(b - a for a, b in zip(lo, hi))
+    _, _, uc = oracle.forward(shape, w.spacing, SO, w.dt, T, w.m[sl].astype(np.float64), src_xyz=w.src_xyz,
+                              wavelet=w.wavelet[N1:N1 + T].astype(np.float32).astype(np.float64),
+                              u_prev0=A[0][sl].astype(np.float64), u_cur0=A[1][sl].astype(np.float64),
+                              sponge_width=w.sponge_width, sponge_faces=w.sponge_faces, vmax=w.vmax,
+                              origin=tuple(lo), global_shape=(N, N, N))
+    return uc[tuple(c - a for c, a in zip(p, lo))], float(np.abs(uc).max())
+
+
+@pytest.mark.parametrize("T", [1, 2])
+def test_full_size_pass_vs_oracle_at_sampled_points(state, oracle, T):
+    w, A, out = state
+    rng = np.random.default_rng(40 + T)
+    got, ref, scale = [], [], []
+    for p in _samples(w, rng):
+        o, s = _oracle_at(oracle, w, A, p, T)
+        got.append(float(out[T][p]))
+        ref.append(o)
+        scale.append(s)
+    got, ref, scale = np.array(got), np.array(ref), np.array(scale)
+    assert np.abs(ref).max() > 0.0  # the checked pass carries a wavefield
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    assert np.all(np.abs(got - ref) <= 1e-5 * np.maximum(scale, 1e-30))
+
+
+def test_full_size_two_one_step_passes_equal_one_t2_pass(state):
+    _, _, out = state
+    assert np.array_equal(out["T1x2"], out[2])
