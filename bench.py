@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--grid", type=int, default=None,
+                    help="grid edge (tiled512: n^3, default 512; so16: n x n x n/2, default 768, receivers scaled)")
     ap.add_argument("--nt", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -125,12 +126,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(load), "power_w_max": max(pw) if pw else None}
 
 
-def kernel_traffic(T):
-    """dram bytes per launch of the pass kernel from the committed ncu summary,
-    only if it was taken on the current kernel source."""
+def kernel_traffic(T, so=8):
+    """dram bytes per grid point per launch of the pass kernel from the
+    committed ncu summary of this space order, only if it was taken on the
+    current kernel source."""
     src = os.path.join(ROOT, "paper_1707_02347_gb300", "csrc", "wave_pass.cuh")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", "tiled_pass_so8_512.md")
+    name = {8: "tiled_pass_so8_512.md", 16: "tiled_pass_so16_768.md"}.get(so)
+    if name is None:
+        return None, h
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None, h
     txt = open(path).read()
@@ -152,7 +157,7 @@ def run_reference(args, rank):
     from paper_1707_02347_gb300 import inputs
 
     oracle.build()
-    n = args.grid
+    n = args.grid or 512
     w = inputs.layered_forward((n, n, n), 8, max(args.nt, 2), seed=1, f=15.0, h=10.0, sponge_width=10,
                                nrec_line=512)
     nt_s = 2
@@ -367,11 +372,13 @@ def main():
     if args.workload == "gradient":
         run_gradient(args, W, inputs, dev, world, rank, dist)
         return
-    n = args.grid
+    n = args.grid or 512
     if args.workload == "so16":
-        w = inputs.high_order_forward(nt=min(args.nt, 500))
-        workload_name = ("high-order forward 768x768x384, h=12.5 m, SO16, %d steps, layered + perturbed model "
-                         "(seed 2), 501x501 surface receivers at 25 m (trilinear)" % w.nt)
+        g = args.grid or 768
+        side = 501 if g == 768 else max(64, g * 501 // 768)
+        w = inputs.high_order_forward(nt=min(args.nt, 500), shape=(g, g, g // 2), n_side=side)
+        workload_name = ("high-order forward %dx%dx%d, h=12.5 m, SO16, %d steps, layered + perturbed model "
+                         "(seed 2), %dx%d surface receivers at 25 m (trilinear)" % (g, g, g // 2, w.nt, side, side))
         so = 16
     else:
         so = args.so
@@ -457,7 +464,7 @@ def main():
     bytes_per_launch = 20.0 * npts  # read u, v, kappa; write u, v (once per pass)
     avg_launch_s = (pass_ms / max(nl, 1)) * 1e-3
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    traffic_pp, src_hash = kernel_traffic(T) if so == 8 else (None, kernel_traffic(T)[1])
+    traffic_pp, src_hash = kernel_traffic(T, so)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic_pp * npts if traffic_pp is not None else None,
             "kernel": "pass_kernel<%d,%d> (SO%d, T=%d)" % (so // 2, T, so, T), "peak_kind": peak_kind,

@@ -118,11 +118,10 @@ wave_status wave_set_sources(wave_plan_t plan, int nsrc, const double* xyz, cons
  * trilinear interpolation of u^{n+1} (the field produced by update n).
  * nrec = 0 clears them.  A dense receiver surface (at least 4096 receivers
  * whose taps all lie in one or two adjacent z quads, e.g. a grid of
- * receivers at one depth) is recorded in capture mode: the pass kernel stores
- * those z quads whole and the traces are gathered after every pass, with the
- * same taps, weights and summation order as the per-tap path (the traces are
- * identical).  Capture mode holds a device buffer of max-T slices
- * [nx][ny][quads][4] floats. */
+ * receivers at one depth) is recorded, when the plan's passes are one-step,
+ * by a gather after every pass from the new field, with the same taps,
+ * weights and summation order as the per-tap path (the traces are
+ * identical). */
 wave_status wave_set_receivers(wave_plan_t plan, int nrec, const double* xyz);
 
 /* Force the tiling of the forward passes (see wave_tiling); T = 1 selects the

@@ -54,10 +54,13 @@ bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std:
     G.bz = t.bz;
     G.xc = std::min(t.xc, nx);
     const int halo = R * (t.T - 1);  // overlapped halo of step 1
+    const bool skew = t.unroll == 4;  // skewed wavefront tiling in y (T = 2 only)
+    if (skew && t.T != 2) return no("the skewed wavefront variant has T = 2");
+    if (skew && t.by < 2 * R) return no("the skewed wavefront variant needs by >= SO");
     G.zlead = -round_up(halo, 4);
     G.b_cols = round_up(t.bz + halo, 4) - G.zlead;
     G.qz = G.b_cols / 4;
-    G.r1y = t.by + 2 * halo;
+    G.r1y = skew ? t.by + halo : t.by + 2 * halo;  // skewed: the tile shifts by r per step
     G.b_rows = G.r1y;
     const int ZH = round_up(R, 4);
     G.a_rows = G.r1y + 2 * R;
@@ -71,7 +74,7 @@ bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std:
                   (t.unroll ? " (unrolled)" : ""));
     G.smem = G.shape ? G.shape->smem : 0;
     if (G.smem > 227 * 1024) return no("tile needs " + std::to_string(G.smem) + " bytes of shared memory");
-    G.nty = (ny + t.by - 1) / t.by;
+    G.nty = skew ? (ny + R + t.by - 1) / t.by : (ny + t.by - 1) / t.by;
     G.ntz = (nzp + t.bz - 1) / t.bz;
     G.nxs = (nx + G.xc - 1) / G.xc;
     G.blocks = static_cast<long long>(G.nty) * G.ntz * G.nxs;
@@ -80,11 +83,11 @@ bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std:
     return true;
 }
 
-// The compiled shape (qz, r1y) as an output tile (by, bz) for radius R and T.
-static bool shape_tile(int R, int T, int qz, int ry, int* by, int* bz)
+// The compiled shape (qz, r1y) of a variant as an output tile (by, bz) for radius R and T.
+static bool shape_tile(int R, int T, int qz, int ry, int variant, int* by, int* bz)
 {
     const int halo = R * (T - 1);
-    *by = ry - 2 * halo;
+    *by = variant == 4 ? ry - halo : ry - 2 * halo;
     // largest bz (multiple of 4) with round_up(bz + halo, 4) + round_up(halo, 4) == 4 qz
     *bz = 0;
     for (int b = 4; b <= 4 * qz; b += 4)
@@ -99,7 +102,8 @@ wave_tiling default_tiling(const int grid[3], int R, int T)
     int n = 0;
     const PassShape* s = pass_shapes(&n);
     for (int i = 0; i < n; ++i)
-        if (s[i].R == R && s[i].T == T && s[i].unroll == 0 && shape_tile(R, T, s[i].qz, s[i].ry, &t.by, &t.bz))
+        if (s[i].R == R && s[i].T == T && s[i].unroll == 0 &&
+            shape_tile(R, T, s[i].qz, s[i].ry, 0, &t.by, &t.bz))
             return t;
     return wave_tiling{T, 0, 0, 0, 0};
 }
@@ -114,7 +118,7 @@ std::vector<wave_tiling> tiling_candidates(const int grid[3], int R)
     for (int i = 0; i < n; ++i) {
         if (s[i].R != R) continue;
         int by, bz;
-        if (!shape_tile(R, s[i].T, s[i].qz, s[i].ry, &by, &bz)) continue;
+        if (!shape_tile(R, s[i].T, s[i].qz, s[i].ry, s[i].unroll, &by, &bz)) continue;
         for (int xc : slabs) {
             wave_tiling t{s[i].T, by, bz, std::min(xc, grid[0]), s[i].unroll};
             PassGeom g;
@@ -147,6 +151,12 @@ static bool verify_schedule(const int grid[3], int R, const wave_tiling& t, int 
 {
     PassGeom g;
     if (!make_geom(grid, R, t, &g, why, false)) return false;
+    if (t.unroll == 4) {
+        // tiles of the skewed variant read each other's values; this model
+        // checks independent overlapped tiles only
+        if (why) *why = "the skewed wavefront variant is not modelled here";
+        return false;
+    }
     const int nx = grid[0], ny = grid[1], nz = grid[2];
     const int T = t.T;
     // geometry under test: the thread region carries halo_per_step (T-1) rows

@@ -120,36 +120,31 @@ void build_receiver_csr(int nrec, const double* xyz, const double h[3], const in
     for (int c = 0; c < ncols; ++c) out->ptr[c + 1] += out->ptr[c];
 }
 
-// Capture plan of a dense receiver surface: when every tap of every receiver
-// lies in at most two adjacent z quads, the pass kernel can store those quads
-// whole (coalesced) and the traces are gathered afterwards.  idx[t] is the
-// float offset of tap t (receiver order, as tw) within one step's capture
-// slice [nx][ny][nq][4].  False (no plan) for fewer than min_rec receivers,
-// taps in more than two quads, or a slice over 2^31 floats.
-bool receiver_capture_plan(int nrec, const double* xyz, const double h[3], const int n[3], int min_rec, int* q0,
-                           int* nq, std::vector<int>* idx)
+// Gather plan of a dense receiver surface: when every tap of every receiver
+// lies in at most two adjacent z quads (a surface or a line of receivers at
+// one depth), each column quad holding taps has them on almost every plane,
+// and recording them tap by tap inside the pass stalls every warp on the same
+// planes; one-step passes gather the traces from the field after the pass
+// instead.  idx[t] is the padded-layout index of tap t (receiver order, as
+// tw).  False for fewer than min_rec receivers, taps in more than two quads,
+// or a padded grid of 2^31 points or more.
+bool receiver_gather_plan(int nrec, const double* xyz, const double h[3], const int n[3], int nzp, int min_rec,
+                          std::vector<int>* idx)
 {
     if (nrec < min_rec) return false;
+    if (static_cast<long long>(n[0]) * n[1] * nzp >= 0x7fffffffLL) return false;
     int qlo = INT_MAX, qhi = -1;
-    std::vector<Tap> all;
+    idx->clear();
     for (int r = 0; r < nrec; ++r) {
         Tap t[8];
         const int c = trilinear_taps(xyz + 3 * r, h, n, t);
         for (int j = 0; j < c; ++j) {
-            all.push_back(t[j]);
+            idx->push_back((t[j].i * n[1] + t[j].j) * nzp + t[j].k);
             qlo = std::min(qlo, t[j].k / 4);
             qhi = std::max(qhi, t[j].k / 4);
         }
     }
-    if (all.empty() || qhi - qlo > 1) return false;
-    const int q = qhi - qlo + 1;
-    if (static_cast<long long>(n[0]) * n[1] * q * 4 > 0x7fffffffLL) return false;
-    idx->resize(all.size());
-    for (size_t t = 0; t < all.size(); ++t)
-        (*idx)[t] = ((all[t].i * n[1] + all[t].j) * q + (all[t].k / 4 - qlo)) * 4 + all[t].k % 4;
-    *q0 = qlo;
-    *nq = q;
-    return true;
+    return !idx->empty() && qhi - qlo <= 1;
 }
 
 // Sponge (the paper's `damp` array, whose profile it does not give): for a

@@ -64,15 +64,13 @@ struct TapSet {
     int2* rec_ent = nullptr;
     int* rec_tptr = nullptr;
     float* rec_tw = nullptr;
-    // capture mode (dense receiver surface): per tap its offset in a step's
-    // capture slice; nullptr = receivers are recorded through the CSR
-    int* cap_idx = nullptr;
-    int cap_q0 = 0, cap_nq = 0;
-    long long cap_slice = 0;
+    // dense receiver surface: per tap its index in the padded layout, for
+    // gathering traces after one-step passes (nullptr = no gather plan)
+    int* gidx = nullptr;
     void release()
     {
         cudaFree(src_ptr); cudaFree(src_ent); cudaFree(rec_ptr); cudaFree(rec_ent); cudaFree(rec_tptr); cudaFree(rec_tw);
-        cudaFree(cap_idx);
+        cudaFree(gidx);
         *this = TapSet();
     }
 };
@@ -131,8 +129,12 @@ struct wave_plan_s {
     bool adj_ready = false;
     float* slots = nullptr;
     size_t slots_floats = 0;
-    float* capbuf = nullptr;  // capture slices of one pass (capture mode)
-    size_t cap_floats = 0;
+    // skewed wavefront variant: exchange planes and progress words of its tiles
+    float* exch = nullptr;
+    size_t exch_floats = 0;
+    int* sync = nullptr;
+    size_t sync_ints = 0;
+    int sm_count = 1;
     // coefficients
     float c0 = 0.f, cx[kMaxR] = {}, cy[kMaxR] = {}, cz[kMaxR] = {};
     // tiling
@@ -254,8 +256,11 @@ PassArgs base_args(wave_plan_t p, const PassGeom& g, const TapSet& taps, const f
 // One pass of g.T steps from the state (u^n0, v^{n0-1/2}); writes
 // (u^{n0+T}, v^{n0+T-1/2}) to (out_u, out_v).  out_v may alias v only when
 // g.T == 1 (each point's increment is read and written by the same thread).
+// gather: slots is the trace array [nt][nrec] and the traces of this
+// one-step pass are gathered from out_u after it (dense receiver surfaces);
+// otherwise slots holds tap values [nt][ntaps], reduced after the run.
 wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const float* wavelet, float* slots, int n0,
-                     const float* u, const float* v, float* out_u, float* out_v)
+                     const float* u, const float* v, float* out_u, float* out_v, bool gather = false)
 {
     const CUtensorMap* mA = get_map(p, u, g.a_rows, g.a_cols);
     const CUtensorMap* mV = get_map(p, v, g.b_rows, g.b_cols);
@@ -265,16 +270,8 @@ wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const
     a.n0 = n0;
     a.out_u = out_u;
     a.out_v = out_v;
-    // capture mode: slots is the trace array [nt][nrec]; the kernel stores the
-    // receivers' z quads whole, and the traces of the pass are gathered after it
-    const bool capture = taps.cap_idx && slots && taps.nrec > 0;
-    if (capture) {
-        a.rec_ptr = nullptr;
-        a.cap = p->capbuf;
-        a.cap_slice = taps.cap_slice;
-        a.cap_q0 = taps.cap_q0;
-        a.cap_nq = taps.cap_nq;
-    }
+    gather = gather && taps.gidx && slots && taps.nrec > 0 && g.T == 1;
+    if (gather) a.rec_ptr = nullptr;
     cudaError_t e = cudaSuccess;
     if (p->prof) {
         if (p->ev_used + 2 > p->ev.size()) {
@@ -287,11 +284,21 @@ wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const
         CK(cudaEventRecord(p->ev[p->ev_used], p->st));
     }
     if (!g.shape) return fail(WAVE_ERR_ARG, "no compiled kernel for this tile shape");
-    e = g.shape->launch(*mA, *mV, *mK, a, g.block, g.smem, g.blocks, p->st);
+    long long blocks = g.blocks;
+    if (g.shape->unroll == 4) {
+        // skewed wavefront: persistent blocks (one per SM) take the tiles in order
+        a.exch = p->exch;
+        a.sync = p->sync;
+        a.nitems = static_cast<int>(g.blocks);
+        a.exch_nit = g.xc + 4 * p->R;
+        CK(cudaMemsetAsync(p->sync, 0, (g.blocks + 1) * sizeof(int), p->st));
+        blocks = std::min<long long>(g.blocks, p->sm_count);
+    }
+    e = g.shape->launch(*mA, *mV, *mK, a, g.block, g.smem, blocks, p->st);
     p->launches++;
-    if (capture && e == cudaSuccess) {
-        e = launch_cap_reduce(p->capbuf, taps.cap_slice, taps.cap_idx, taps.rec_tptr, taps.rec_tw,
-                              slots + static_cast<long long>(n0) * taps.nrec, g.T, taps.nrec, p->st);
+    if (gather && e == cudaSuccess) {
+        e = launch_rec_gather(out_u, taps.gidx, taps.rec_tptr, taps.rec_tw, slots + static_cast<long long>(n0) * taps.nrec,
+                              taps.nrec, p->st);
         p->launches++;
     }
     if (p->prof) {
@@ -309,10 +316,10 @@ struct Fields {
 
 // One pass of g.T steps on the state f.
 wave_status step_pass(wave_plan_t p, const PassGeom& g, Fields* f, const TapSet& taps, const float* wavelet,
-                      float* slots, int n0)
+                      float* slots, int n0, bool gather = false)
 {
     if (g.T == 1) {
-        wave_status s = run_pass(p, g, taps, wavelet, slots, n0, f->u, f->v, f->f0, f->v);
+        wave_status s = run_pass(p, g, taps, wavelet, slots, n0, f->u, f->v, f->f0, f->v, gather);
         if (s) return s;
         std::swap(f->u, f->f0);  // u <- new, f0 <- old u; v updated in place
         return WAVE_OK;
@@ -327,7 +334,7 @@ wave_status step_pass(wave_plan_t p, const PassGeom& g, Fields* f, const TapSet&
 // Advance `steps` steps from level n0 with the plan's tiling (T > 1 passes
 // while they fit, then one-step passes).
 wave_status advance(wave_plan_t p, Fields* f, const TapSet& taps, const float* wavelet, float* slots, int n0,
-                    int steps, bool use_tiling)
+                    int steps, bool use_tiling, bool gather = false)
 {
     int n = n0;
     const int end = n0 + steps;
@@ -340,7 +347,7 @@ wave_status advance(wave_plan_t p, Fields* f, const TapSet& taps, const float* w
     }
     const PassGeom& g1 = (use_tiling && p->geom.T == 1) ? p->geom : p->geom1;
     while (n < end) {
-        wave_status s = step_pass(p, g1, f, taps, wavelet, slots, n);
+        wave_status s = step_pass(p, g1, f, taps, wavelet, slots, n, gather);
         if (s) return s;
         n += 1;
     }
@@ -356,21 +363,14 @@ wave_status finish(wave_plan_t p)
     return WAVE_OK;
 }
 
-// Receivers at least this many, all in one or two z quads: capture mode.
-constexpr int kCaptureMinReceivers = 4096;
-
-int max_pass_T()
-{
-    int n = 0, T = 1;
-    const PassShape* s = pass_shapes(&n);
-    for (int i = 0; i < n; ++i) T = std::max(T, s[i].T);
-    return T;
-}
+// Receivers at least this many, all in one or two z quads: traces gathered
+// after one-step passes.
+constexpr int kGatherMinReceivers = 4096;
 
 // Taps of the sources and receivers of one direction (the adjoint swaps
-// them); allow_capture lets a dense receiver surface use capture mode.
+// them); allow_gather lets a dense receiver surface use the gather plan.
 wave_status build_taps(wave_plan_t p, TapSet* t, int nsrc, const double* sxyz, int nrec, const double* rxyz,
-                       bool allow_capture)
+                       bool allow_gather)
 {
     t->release();
     p->gen++;
@@ -389,21 +389,8 @@ wave_status build_taps(wave_plan_t p, TapSet* t, int nsrc, const double* sxyz, i
     CK(upload(&t->rec_tptr, tptr.data(), tptr.size() * 4, p->st));
     CK(upload(&t->rec_tw, tw.data(), tw.size() * 4, p->st));
     std::vector<int> idx;
-    int q0 = 0, nq = 0;
-    if (allow_capture && receiver_capture_plan(nrec, rxyz, p->h, p->n, kCaptureMinReceivers, &q0, &nq, &idx)) {
-        CK(upload(&t->cap_idx, idx.data(), idx.size() * 4, p->st));
-        t->cap_q0 = q0;
-        t->cap_nq = nq;
-        t->cap_slice = static_cast<long long>(p->n[0]) * p->n[1] * nq * 4;
-        const size_t need = static_cast<size_t>(t->cap_slice) * max_pass_T();
-        if (need > p->cap_floats) {
-            cudaFree(p->capbuf);
-            p->capbuf = nullptr;
-            p->cap_floats = 0;
-            CK(cudaMalloc(&p->capbuf, need * 4));
-            p->cap_floats = need;
-        }
-    }
+    if (allow_gather && receiver_gather_plan(nrec, rxyz, p->h, p->n, p->nzp, kGatherMinReceivers, &idx))
+        CK(upload(&t->gidx, idx.data(), idx.size() * 4, p->st));
     return WAVE_OK;
 }
 
@@ -436,6 +423,25 @@ wave_status apply_tiling(wave_plan_t p, const wave_tiling& t)
     PassGeom g;
     std::string why;
     if (!make_geom(p->n, p->R, t, &g, &why)) return fail(WAVE_ERR_ARG, "tiling rejected: " + why);
+    if (g.shape && g.shape->unroll == 4) {
+        // exchange: per tile, every plane of its slab, 3r rows of 4 qz floats
+        const size_t need = static_cast<size_t>(g.blocks) * (g.xc + 4 * p->R) * 3 * p->R * 4 * g.qz;
+        if (need > p->exch_floats) {
+            cudaFree(p->exch);
+            p->exch = nullptr;
+            p->exch_floats = 0;
+            CK(cudaMalloc(&p->exch, need * 4));
+            p->exch_floats = need;
+        }
+        const size_t nsync = static_cast<size_t>(g.blocks) + 1;
+        if (nsync > p->sync_ints) {
+            cudaFree(p->sync);
+            p->sync = nullptr;
+            p->sync_ints = 0;
+            CK(cudaMalloc(&p->sync, nsync * 4));
+            p->sync_ints = nsync;
+        }
+    }
     p->tiling = t;
     p->geom = g;
     p->gen++;
@@ -516,7 +522,8 @@ void destroy(wave_plan_t p)
     cudaFree(p->stage_r);
     for (auto* l : p->levels) cudaFree(l);
     cudaFree(p->work);
-    cudaFree(p->capbuf);
+    cudaFree(p->exch);
+    cudaFree(p->sync);
     for (auto e : p->ev) cudaEventDestroy(e);
     delete p;
 }
@@ -533,20 +540,21 @@ wave_status forward_impl(wave_plan_t p, const float* u_init, float* rec_out, flo
         CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
         CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
     }
-    // receivers: tap values into slots, reduced at the end; in capture mode
-    // the traces are gathered into rec_out after every pass
-    const bool capture = p->fwd.cap_idx && p->fwd.nrec > 0 && p->nt > 0;
+    // receivers: tap values into slots, reduced at the end; for a dense
+    // receiver surface and one-step passes the traces are gathered into
+    // rec_out after every pass
+    const bool gather = p->fwd.gidx && p->fwd.nrec > 0 && p->nt > 0 && p->geom.T == 1;
     float* slots = nullptr;
-    if (capture) {
+    if (gather) {
         slots = rec_out;
     } else if (p->fwd.nrec > 0 && p->fwd.ntaps > 0) {
         wave_status s = ensure_slots(p, static_cast<size_t>(p->nt) * p->fwd.ntaps);
         if (s) return s;
         slots = p->slots;
     }
-    wave_status s = advance(p, &f, p->fwd, p->wavelet, slots, 0, p->nt, true);
+    wave_status s = advance(p, &f, p->fwd, p->wavelet, slots, 0, p->nt, true, gather);
     if (s) return s;
-    if (p->fwd.nrec > 0 && p->nt > 0 && !capture) {
+    if (p->fwd.nrec > 0 && p->nt > 0 && !gather) {
         if (p->fwd.ntaps > 0)
             CKL(launch_rec_reduce(slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec_out, p->nt, p->fwd.nrec, p->fwd.ntaps,
                                  p->st));
@@ -619,6 +627,8 @@ extern "C" wave_status wave_plan_create(wave_plan_t* out, const int grid[3], con
     auto* p = new wave_plan_s();
     p->dev = dev;
     p->st = static_cast<cudaStream_t>(o.stream);
+    if (cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || p->sm_count < 1)
+        p->sm_count = 1;
     p->opt = o;
     for (int a = 0; a < 3; ++a) {
         p->n[a] = grid[a];
@@ -930,15 +940,15 @@ wave_status gradient_enqueue(wave_plan_t p, const GradPlan& gp, const float* d_o
     Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
     CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
     CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
-    const bool capture = p->fwd.cap_idx != nullptr;  // traces gathered into rec after every pass
+    const bool gather = p->fwd.gidx != nullptr && p->geom.T == 1;  // traces gathered into rec after every pass
     for (int c = 0; c < nseg; ++c) {
         CK(cudaMemcpyAsync(ck[2 * c], f.u, p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
         CK(cudaMemcpyAsync(ck[2 * c + 1], f.v, p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
         const int steps = std::min(K, nt - c * K);
-        s = advance(p, &f, p->fwd, p->wavelet, capture ? rec : p->slots, c * K, steps, true);
+        s = advance(p, &f, p->fwd, p->wavelet, gather ? rec : p->slots, c * K, steps, true, gather);
         if (s) return s;
     }
-    if (!capture) {
+    if (!gather) {
         if (p->fwd.ntaps > 0)
             CKL(launch_rec_reduce(p->slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec, nt, nrec, p->fwd.ntaps, p->st));
         else
@@ -1148,7 +1158,7 @@ wave_status batch_capture(wave_batch_t b, float* const* rec_out)
         if (p->fwd.nrec > 0 && p->nt > 0 && (!rec_out || !rec_out[i]))
             return fail(WAVE_ERR_ARG, "wave_batch_forward: a shot with receivers has no rec_out");
         // everything forward_impl would allocate is allocated before the capture
-        if (p->fwd.nrec > 0 && p->fwd.ntaps > 0 && !p->fwd.cap_idx) {
+        if (p->fwd.nrec > 0 && p->fwd.ntaps > 0 && !(p->fwd.gidx && p->geom.T == 1)) {
             wave_status s = ensure_slots(p, static_cast<size_t>(p->nt) * p->fwd.ntaps);
             if (s) return s;
         }

@@ -64,11 +64,10 @@ void build_source_csr(int nsrc, const double* xyz, const double h[3], const int 
 void build_receiver_csr(int nrec, const double* xyz, const double h[3], const int n[3], int nzp, ColumnCsr* out,
                         std::vector<int>* tptr, std::vector<float>* tw);
 
-// Capture plan of a dense receiver surface (taps in at most two adjacent z
-// quads, at least min_rec receivers): first quad, quad count, and per tap its
-// float offset in one step's slice [nx][ny][nq][4].
-bool receiver_capture_plan(int nrec, const double* xyz, const double h[3], const int n[3], int min_rec, int* q0,
-                           int* nq, std::vector<int>* idx);
+// Gather plan of a dense receiver surface (taps in at most two adjacent z
+// quads, at least min_rec receivers): per tap its index in the padded layout.
+bool receiver_gather_plan(int nrec, const double* xyz, const double h[3], const int n[3], int nzp, int min_rec,
+                          std::vector<int>* idx);
 
 // Sponge profile of one axis (1/ms), in double, rounded to float by the caller.
 void sponge_profile(int n, int width, bool lo, bool hi, double dmax, std::vector<float>* out, int padded_n);

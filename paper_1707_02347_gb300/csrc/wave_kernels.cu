@@ -65,20 +65,16 @@ __global__ void rec_reduce_kernel(const float* __restrict__ slots, const int* __
     }
 }
 
-// Traces of one pass from the captured quads: the taps of each receiver in
-// the order (and with the arithmetic) of rec_reduce_kernel.
-__global__ void cap_reduce_kernel(const float* __restrict__ cap, long long slice, const int* __restrict__ cap_idx,
+// One trace row gathered from a field after a one-step pass: the taps of
+// each receiver in the order (and with the arithmetic) of rec_reduce_kernel.
+__global__ void rec_gather_kernel(const float* __restrict__ u, const int* __restrict__ gidx,
                                   const int* __restrict__ tptr, const float* __restrict__ tw, float* __restrict__ rec,
-                                  int T, int nrec)
+                                  int nrec)
 {
-    const long long n = static_cast<long long>(T) * nrec;
-    for (long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; p < n;
-         p += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int j = static_cast<int>(p % nrec);
-        const float* c = cap + (p / nrec) * slice;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrec; j += gridDim.x * blockDim.x) {
         float acc = 0.f;
-        for (int t = tptr[j]; t < tptr[j + 1]; ++t) acc = __fmaf_rn(tw[t], c[cap_idx[t]], acc);
-        rec[p] = acc;
+        for (int t = tptr[j]; t < tptr[j + 1]; ++t) acc = __fmaf_rn(tw[t], u[gidx[t]], acc);
+        rec[j] = acc;
     }
 }
 
@@ -202,11 +198,10 @@ const PassShape* find_pass_shape(int R, int T, int qz, int ry, int unroll)
     return nullptr;
 }
 
-cudaError_t launch_cap_reduce(const float* cap, long long slice, const int* cap_idx, const int* tptr, const float* tw,
-                              float* rec, int T, int nrec, cudaStream_t st)
+cudaError_t launch_rec_gather(const float* u, const int* gidx, const int* tptr, const float* tw, float* rec, int nrec,
+                              cudaStream_t st)
 {
-    cap_reduce_kernel<<<grid_for(static_cast<long long>(T) * nrec, 256), 256, 0, st>>>(cap, slice, cap_idx, tptr, tw,
-                                                                                      rec, T, nrec);
+    rec_gather_kernel<<<grid_for(nrec, 256), 256, 0, st>>>(u, gidx, tptr, tw, rec, nrec);
     return cudaGetLastError();
 }
 

@@ -42,20 +42,24 @@ struct PassArgs {
     float* slots;           // [rows][ntaps]
     int ntaps;
     int slot_row0;          // rec row stored in slot row 0
-    // dense receiver surfaces (capture mode, receivers not in the CSR): the
-    // output quads of z quads [cap_q0, cap_q0 + cap_nq) are stored whole, step
-    // k of the pass at cap + k * cap_slice + ((x * ny + y) * cap_nq + q) * 4
-    float* cap;
-    long long cap_slice;
-    int cap_q0, cap_nq;
-    int* err;               // device error word (bit 0: a bounded wait gave up)
+    // skewed wavefront tiling (variant 4): tile j of a column of y tiles
+    // takes the top rows of tile j-1's first step from `exch` once tile j-1's
+    // progress word says the plane is there.  sync: [nitems] progress words
+    // (iterations completed) then the work counter; exch: [nitems][exch_nit]
+    // [3 r][4 qz] floats per tile.
+    float* exch;
+    int* sync;
+    int nitems;
+    int exch_nit;
+    int* err;               // device error word (bit 0: a bounded wait gave up; bit 1: a tile waited too long for its neighbour)
 };
 
 // One compiled instantiation of the pass kernel: radius R, T steps, thread
 // blocks of `ry` rows by `qz` z quads, its shared memory and its launcher.
 struct PassShape {
     int R, T, qz, ry;
-    int unroll;  // x-queue storage: 0 = registers (moved), 1 = registers (loop unrolled), 2 = tensor memory
+    int unroll;  // variant: x-queue storage 0 = registers (moved), 1 = registers (loop unrolled),
+                 // 2 = tensor memory; 4 = skewed wavefront tiling in y (T = 2, tensor memory)
     size_t smem;
     cudaError_t (*launch)(const CUtensorMap& mapA, const CUtensorMap& mapV, const CUtensorMap& mapK,
                           const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st);
@@ -78,10 +82,11 @@ cudaError_t launch_final_state(const float* u, const float* v, float* u2, int nx
                                cudaStream_t st);
 cudaError_t launch_rec_reduce(const float* slots, const int* tptr, const float* tw, float* rec, int rows,
                               int nrec, int ntaps, cudaStream_t st);
-// rec[k][j] = sum over the taps t of receiver j (in order) of tw[t] * cap[k * slice + cap_idx[t]], k < T:
-// the same sums in the same order as launch_rec_reduce, from the captured quads of one pass.
-cudaError_t launch_cap_reduce(const float* cap, long long slice, const int* cap_idx, const int* tptr, const float* tw,
-                              float* rec, int T, int nrec, cudaStream_t st);
+// rec[j] = sum over the taps t of receiver j (in order) of tw[t] * u[gidx[t]]: one trace row
+// gathered from a field in the padded layout, the same sums in the same order as
+// launch_rec_reduce.
+cudaError_t launch_rec_gather(const float* u, const int* gidx, const int* tptr, const float* tw, float* rec, int nrec,
+                              cudaStream_t st);
 // grad -= scale * mu * (v_new - v_old)   (scale = 1/dt^2)
 cudaError_t launch_grad_accum(float* grad, const float* mu, const float* v_new, const float* v_old, long long n,
                               float scale, cudaStream_t st);

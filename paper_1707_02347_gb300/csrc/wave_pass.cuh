@@ -550,22 +550,10 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
             if (wr_hi >= k * R && wr_lo < RY - k * R) wsteps = k + 1;
     }
 
-    // sparse events per step.  Sources: cursor and x of the next source tap in
-    // this column.  Receivers: cursor and the next two entries themselves,
-    // loaded one event ahead, so that recording a plane's taps needs no
-    // dependent global load (every column of a receiver surface has events
-    // on the same planes, and the whole block would wait on them).
-    const int2 none = make_int2(INT_MAX, 0);
-    int scur[T], snxt[T], rcur[T], send = 0, rend = 0;
-    int2 rq0[T], rq1[T];
+    // sparse events per step: next x with a source or receiver tap in this column
+    int scur[T], rcur[T], nxt[T], send = 0, rend = 0;
 #pragma unroll
-    for (int k = 0; k < T; ++k) {
-        scur[k] = 0;
-        snxt[k] = INT_MAX;
-        rcur[k] = 0;
-        rq0[k] = none;
-        rq1[k] = none;
-    }
+    for (int k = 0; k < T; ++k) { scur[k] = 0; rcur[k] = 0; nxt[k] = INT_MAX; }
     // (cursors always start inside the column's own CSR range [lo, end))
     if (colv && a.src_ptr != nullptr) {
         const int lo = a.src_ptr[col];
@@ -573,19 +561,17 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
 #pragma unroll
         for (int k = 0; k < T; ++k) {
             scur[k] = lo < send ? first_at_or_after(a.src_ent, lo, send, X0 - R * (T - 1 - k)) : send;
-            if (scur[k] < send) snxt[k] = a.src_ent[scur[k]].x;
+            if (scur[k] < send) nxt[k] = a.src_ent[scur[k]].x;
         }
     }
     if (own && a.rec_ptr != nullptr) {
         const int lo = a.rec_ptr[col];
         rend = a.rec_ptr[col + 1];
         const int c0 = lo < rend ? first_at_or_after(a.rec_ent, lo, rend, X0) : rend;
-        const int2 e0 = c0 < rend ? a.rec_ent[c0] : none, e1 = c0 + 1 < rend ? a.rec_ent[c0 + 1] : none;
 #pragma unroll
         for (int k = 0; k < T; ++k) {
             rcur[k] = c0;
-            rq0[k] = e0;
-            rq1[k] = e1;
+            if (c0 < rend) nxt[k] = min(nxt[k], a.rec_ent[c0].x);
         }
     }
 
@@ -764,7 +750,7 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
                         laplacian_x<R>(u, xq, a, xl, xh);
                     }
                     float4 L = combine(yl, yh, zl, zh, xl, xh);
-                    if (xk == snxt[k]) {
+                    if (xk == nxt[k]) {
                         // sources of this plane (before the update) ...
                         int c = scur[k];
                         while (c < send) {
@@ -779,40 +765,27 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
                             ++c;
                         }
                         scur[k] = c;
-                        snxt[k] = c < send ? a.src_ent[c].x : INT_MAX;
                     }
                     float4 v = (k == 0) ? lds4(pb + posB) : vring[((k - 1) * NV + vread) * NTHR + tid];
                     const float4 kp = (k == 0) ? lds4(pb + bfl + posB) : kpre[k];
                     const float dx = (xk < a.dxlo || xk >= a.dxhi) ? a.damp_x[min(max(xk, 0), a.nx - 1)] : 0.f;
                     update4(L, u, v, kp, dx, dyz, dyz_zero, a.inv2dt);
-                    if (a.cap != nullptr && own && xk >= X0 && xk < X1) {
-                        // capture mode: the receivers' z quads stored whole (coalesced)
-                        const int qi = (gz >> 2) - a.cap_q0;
-                        if (qi >= 0 && qi < a.cap_nq)
-                            *reinterpret_cast<float4*>(
-                                a.cap + k * a.cap_slice +
-                                ((static_cast<long long>(xk) * a.ny + gy) * a.cap_nq + qi) * 4) = u;
-                    }
-                    if (xk == rq0[k].x) {
-                        // ... and receivers (after it): the two prefetched
-                        // entries, then (rarely) further ones of this plane;
-                        // then prefetch the next two
-                        float* srow = a.slots + static_cast<long long>(a.n0 + k - a.slot_row0) * a.ntaps;
-                        int c = rcur[k] + 1;
-                        if (xk < X1) srow[rq0[k].y >> 2] = lane_of(u, rq0[k].y & 3);
-                        if (rq1[k].x == xk) {
-                            if (xk < X1) srow[rq1[k].y >> 2] = lane_of(u, rq1[k].y & 3);
+                    if (xk == nxt[k]) {
+                        // ... and receivers (after it); then the next event of this step
+                        int c = rcur[k];
+                        while (c < rend) {
+                            const int2 e = a.rec_ent[c];
+                            if (e.x != xk) break;
+                            if (xk < X1)
+                                a.slots[static_cast<long long>(a.n0 + k - a.slot_row0) * a.ntaps + (e.y >> 2)] =
+                                    lane_of(u, e.y & 3);
                             ++c;
-                            while (c < rend) {
-                                const int2 e = a.rec_ent[c];
-                                if (e.x != xk) break;
-                                if (xk < X1) srow[e.y >> 2] = lane_of(u, e.y & 3);
-                                ++c;
-                            }
                         }
                         rcur[k] = c;
-                        rq0[k] = c < rend ? a.rec_ent[c] : none;
-                        rq1[k] = c + 1 < rend ? a.rec_ent[c + 1] : none;
+                        int nx2 = INT_MAX;
+                        if (scur[k] < send) nx2 = a.src_ent[scur[k]].x;
+                        if (rcur[k] < rend) nx2 = min(nx2, a.rec_ent[rcur[k]].x);
+                        nxt[k] = nx2;
                     }
                     prev_u = u;
                     prev_v = v;

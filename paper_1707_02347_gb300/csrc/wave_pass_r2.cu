@@ -1,12 +1,15 @@
 // wave_pass_r2.cu -- instantiations of the pass kernel for stencil radius 2 (SO 4).
 // Each entry is one (T, z quads per row, thread rows, queue storage) variant the
-// autotuner can pick; queue storage 0/1 = registers (moved / rotated), 2 = tensor memory.
-#include "wave_pass.cuh"
+// autotuner can pick; queue storage 0/1 = registers (moved / rotated), 2 = tensor memory;
+// variant 4 = two-step pass with skewed wavefront tiling in y (tensor-memory queues).
+#include "wave_skew.cuh"
 
 namespace wave {
 
 #define WAVE_SHAPE(T, QZ, RY, QM) \
     {2, T, QZ, RY, QM, detail::smem_bytes<2, T, QZ, RY>(), &detail::launch_impl<2, T, QZ, RY, QM>}
+// variant 4: skewed wavefront tiling in y, T = 2, x queues in tensor memory
+#define WAVE_SKEW(QZ, RY) {2, 2, QZ, RY, 4, detail::skew_smem_bytes<2, QZ, RY>(), &detail::launch_skew<2, QZ, RY>}
 
 const PassShape* pass_shapes_r2(int* n)
 {
@@ -32,6 +35,7 @@ const PassShape* pass_shapes_r2(int* n)
         WAVE_SHAPE(4, 16, 24, 0),
         WAVE_SHAPE(4, 8, 32, 1),
         WAVE_SHAPE(4, 8, 32, 2),
+        WAVE_SKEW(16, 32),
     };
     *n = static_cast<int>(sizeof(shapes) / sizeof(shapes[0]));
     return shapes;

@@ -93,11 +93,12 @@ def test_plain_forward_64_so4_vs_oracle(W, oracle):
 @pytest.mark.parametrize("so,shape,tilings", [
     (4, (37, 34, 30), [(1, 16, 64, 11), (2, 28, 24, 9), (3, 24, 24, 40), (4, 12, 48, 13), (1, 16, 64, 37, 1),
                        (2, 12, 56, 30, 1), (3, 24, 24, 19, 1), (1, 16, 64, 37, 2), (2, 28, 56, 30, 2),
-                       (3, 24, 56, 19, 2), (2, 20, 56, 20, 2), (4, 20, 16, 13, 2)]),
+                       (3, 24, 56, 19, 2), (2, 20, 56, 20, 2), (4, 20, 16, 13, 2), (2, 30, 56, 30, 4)]),
     (8, (41, 35, 38), [(1, 32, 32, 40), (2, 24, 24, 10), (2, 16, 56, 41), (3, 16, 16, 17), (1, 32, 32, 41, 1),
                        (1, 16, 64, 23, 1), (2, 16, 56, 41, 1), (2, 24, 24, 29, 1), (3, 16, 16, 40, 1),
                        (1, 8, 64, 41, 2), (1, 16, 64, 23, 2), (2, 16, 56, 41, 2), (2, 24, 56, 29, 2),
-                       (2, 56, 24, 17, 2), (3, 16, 16, 40, 2), (1, 32, 64, 41, 2)]),
+                       (2, 56, 24, 17, 2), (3, 16, 16, 40, 2), (1, 32, 64, 41, 2), (2, 28, 56, 41, 4),
+                       (2, 60, 24, 13, 4)]),
     (16, (36, 33, 34), [(1, 16, 64, 12), (2, 16, 16, 12), (2, 16, 16, 40), (1, 32, 32, 7), (1, 16, 64, 36, 1),
                         (2, 16, 16, 36, 1), (1, 8, 64, 36, 2), (1, 16, 64, 12, 2), (2, 16, 16, 36, 2),
                         (1, 32, 64, 36, 2)]),
@@ -243,3 +244,21 @@ def test_dense_receiver_surface_capture_mode(W, oracle, so):
     w.rec_xyz = surf
     rec_o, _, _ = run_oracle(oracle, w)
     assert rel_l2(cap[0], rec_o) <= TOL
+
+
+@pytest.mark.parametrize("so,tiling", [(8, (2, 28, 56, 12, 4)), (8, (2, 60, 24, 9, 4)), (4, (2, 30, 56, 11, 4))])
+def test_skewed_wavefront_tiles(W, oracle, so, tiling):
+    """Skewed wavefront variant (y tiles shifted by r per step, each tile
+    taking the top rows of the tile below through the exchange buffer) on a
+    grid of several y tiles, x slabs and z tiles: bit-identical to the
+    one-step kernel, fields and traces, and within the parity bar of the
+    oracle."""
+    shape = (31, 95, 130)
+    w = small_layered(shape, so, 19, seed=61 + so, nrec=11)
+    ref_rec, ref_u = run_gpu(W, w, (1, 16, 64, 31))
+    rec, uf = run_gpu(W, w, tiling)
+    assert np.array_equal(rec, ref_rec)
+    assert np.array_equal(uf, ref_u)
+    rec_o, up_o, uc_o = run_oracle(oracle, w)
+    assert rel_l2(uf[1], uc_o) <= TOL
+    assert rel_l2(rec, rec_o) <= TOL

@@ -1,6 +1,9 @@
 """Parity at the full 512^3 SO8 size, in the launch configurations the
 benchmark times (T = 1 and T = 2 passes with the x queues in tensor memory).
 
+The skewed wavefront variant of the two-step pass is checked against the
+same passes bit for bit.
+
 The FP64 oracle cannot run the whole grid, so outputs are checked one by one:
 the GPU runs the workload for n1 steps and keeps the state (u^{n1-1}, u^{n1});
 then it advances one more pass (T steps) from that state.  For each sampled
@@ -43,9 +46,10 @@ def state(oracle):
     _, uA = plan.forward(want_final=True)
     plan.close()
     out = {}
-    for T, tiling in ((1, (1, 8, 64, 64, 2)), (2, (2, 24, 56, 128, 2))):
-        p = W.WavePlan(w.shape, w.spacing, SO, w.dt, T, m, sponge_width=w.sponge_width, vmax=w.vmax, tiling=tiling)
-        p.set_sources(w.src_xyz, torch.from_numpy(wav[N1:N1 + T].copy()).to(dev))
+    for T, tiling in ((1, (1, 8, 64, 64, 2)), (2, (2, 24, 56, 128, 2)), ("skew", (2, 28, 56, 128, 4))):
+        nT = 2 if T == "skew" else T
+        p = W.WavePlan(w.shape, w.spacing, SO, w.dt, nT, m, sponge_width=w.sponge_width, vmax=w.vmax, tiling=tiling)
+        p.set_sources(w.src_xyz, torch.from_numpy(wav[N1:N1 + nT].copy()).to(dev))
         _, uB = p.forward(u_init=uA, want_final=True)
         torch.cuda.synchronize()
         out[T] = uB[1].cpu().numpy()
@@ -113,3 +117,4 @@ def test_full_size_pass_vs_oracle_at_sampled_points(state, oracle, T):
 def test_full_size_two_one_step_passes_equal_one_t2_pass(state):
     _, _, out = state
     assert np.array_equal(out["T1x2"], out[2])
+    assert np.array_equal(out["T1x2"], out["skew"])  # the skewed wavefront variant of the two-step pass
