@@ -256,6 +256,33 @@ PassArgs base_args(wave_plan_t p, const PassGeom& g, const TapSet& taps, const f
 // One pass of g.T steps from the state (u^n0, v^{n0-1/2}); writes
 // (u^{n0+T}, v^{n0+T-1/2}) to (out_u, out_v).  out_v may alias v only when
 // g.T == 1 (each point's increment is read and written by the same thread).
+// Exchange planes and progress words of the skewed wavefront variant for a
+// geometry (grown as needed; a no-op once large enough, so that a pass inside
+// a graph capture never allocates).
+wave_status ensure_skew_buffers(wave_plan_t p, const PassGeom& g)
+{
+    // exchange: per tile, every plane of its slab, 3r rows of 4 qz floats
+    const size_t need = static_cast<size_t>(g.blocks) * (g.xc + 4 * p->R) * 3 * p->R * 4 * g.qz;
+    if (need > p->exch_floats) {
+        cudaFree(p->exch);
+        p->exch = nullptr;
+        p->exch_floats = 0;
+        p->gen++;
+        CK(cudaMalloc(&p->exch, need * 4));
+        p->exch_floats = need;
+    }
+    const size_t nsync = static_cast<size_t>(g.blocks) + 1;
+    if (nsync > p->sync_ints) {
+        cudaFree(p->sync);
+        p->sync = nullptr;
+        p->sync_ints = 0;
+        p->gen++;
+        CK(cudaMalloc(&p->sync, nsync * 4));
+        p->sync_ints = nsync;
+    }
+    return WAVE_OK;
+}
+
 // gather: slots is the trace array [nt][nrec] and the traces of this
 // one-step pass are gathered from out_u after it (dense receiver surfaces);
 // otherwise slots holds tap values [nt][ntaps], reduced after the run.
@@ -287,6 +314,8 @@ wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const
     long long blocks = g.blocks;
     if (g.shape->unroll == 4) {
         // skewed wavefront: persistent blocks (one per SM) take the tiles in order
+        wave_status st = ensure_skew_buffers(p, g);
+        if (st) return st;
         a.exch = p->exch;
         a.sync = p->sync;
         a.nitems = static_cast<int>(g.blocks);
@@ -424,23 +453,8 @@ wave_status apply_tiling(wave_plan_t p, const wave_tiling& t)
     std::string why;
     if (!make_geom(p->n, p->R, t, &g, &why)) return fail(WAVE_ERR_ARG, "tiling rejected: " + why);
     if (g.shape && g.shape->unroll == 4) {
-        // exchange: per tile, every plane of its slab, 3r rows of 4 qz floats
-        const size_t need = static_cast<size_t>(g.blocks) * (g.xc + 4 * p->R) * 3 * p->R * 4 * g.qz;
-        if (need > p->exch_floats) {
-            cudaFree(p->exch);
-            p->exch = nullptr;
-            p->exch_floats = 0;
-            CK(cudaMalloc(&p->exch, need * 4));
-            p->exch_floats = need;
-        }
-        const size_t nsync = static_cast<size_t>(g.blocks) + 1;
-        if (nsync > p->sync_ints) {
-            cudaFree(p->sync);
-            p->sync = nullptr;
-            p->sync_ints = 0;
-            CK(cudaMalloc(&p->sync, nsync * 4));
-            p->sync_ints = nsync;
-        }
+        wave_status st = ensure_skew_buffers(p, g);
+        if (st) return st;
     }
     p->tiling = t;
     p->geom = g;

@@ -262,3 +262,28 @@ def test_skewed_wavefront_tiles(W, oracle, so, tiling):
     rec_o, up_o, uc_o = run_oracle(oracle, w)
     assert rel_l2(uf[1], uc_o) <= TOL
     assert rel_l2(rec, rec_o) <= TOL
+
+
+@pytest.mark.parametrize("so", [4, 8, 16])
+def test_autotune_then_forward(W, oracle, so):
+    """The autotuner times every compiled candidate on the plan's grid (all
+    variants, including the skewed wavefront one, whose buffers it sizes on
+    the way), keeps the fastest, and the tuned plan still matches the
+    one-step kernel bit for bit."""
+    shape = (44, 60, 52)
+    w = small_layered(shape, so, 17, seed=71 + so, nrec=7)
+    ref_rec, ref_u = run_gpu(W, w, (1, 16, 64, 44))
+    dev = torch.device("cuda")
+    m = torch.from_numpy(np.ascontiguousarray(w.m, dtype=np.float32)).to(dev)
+    plan = W.WavePlan(w.shape, w.spacing, w.so, w.dt, w.nt, m, sponge_width=w.sponge_width,
+                      sponge_faces=w.sponge_faces, vmax=w.vmax)
+    plan.set_sources(w.src_xyz, torch.from_numpy(np.ascontiguousarray(w.wavelet, dtype=np.float32)).to(dev))
+    plan.set_receivers(w.rec_xyz)
+    tuned = plan.autotune(passes=1)
+    assert len(tuned) > 3
+    assert any(t[0][4] == 4 for t in tuned) == (so in (4, 8))  # skewed candidates timed where compiled
+    rec, uf = plan.forward(want_final=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(rec.cpu().numpy(), ref_rec)
+    assert np.array_equal(uf.cpu().numpy(), ref_u)
+    plan.close()

@@ -126,3 +126,22 @@ def test_paper_skewed_schedule_order(W):
 ])
 def test_tiling_check_limits(W, tiling, ok):
     assert W.tiling_check((512, 512, 512), 8, tiling) == ok
+
+
+@pytest.mark.parametrize("so,tiling,ok", [
+    # skewed wavefront variant: T = 2 only; a tile is by = rows - r high (one
+    # halo side instead of two), so 32 rows give by = 32 - r
+    (8, (2, 28, 56, 128, 4), True), (8, (2, 60, 24, 128, 4), True), (4, (2, 30, 56, 128, 4), True),
+    (8, (2, 24, 56, 128, 4), False),  # the overlapped shape's by: no compiled skewed kernel
+    (8, (3, 24, 16, 128, 4), False),  # T = 3
+    (16, (2, 24, 16, 128, 4), False),  # no radius-8 skewed kernel
+])
+def test_tiling_check_skewed_variant(W, so, tiling, ok):
+    assert W.tiling_check((512, 512, 512), so, tiling) == ok
+
+
+def test_schedule_verifier_declines_skewed_variant(W):
+    # the brute-force verifier models independent (overlapped) tiles only; the
+    # skewed variant is checked bit for bit against the one-step kernel on the GPU
+    ok, why = W.schedule_verify((40, 36, 44), 8, (2, 28, 56, 16, 4))
+    assert not ok and "skewed" in why
