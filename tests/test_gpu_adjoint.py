@@ -165,3 +165,26 @@ def test_fwi_autograd_function(W, oracle):
     assert float(J) == pytest.approx(J_ref, rel=1e-7)
     assert torch.equal(m.grad, g_ref)
     plan.close()
+
+
+@pytest.mark.parametrize("tiling", [(2, 28, 56, 34, 4), (2, 24, 56, 34, 2), (1, 8, 64, 34, 2)])
+def test_gradient_independent_of_pass_variant(W, oracle, tiling):
+    """The gradient runs its forward and adjoint sweeps with the plan's
+    tiling: the skewed wavefront variant, the tensor-memory T = 2 pass and the
+    one-step pass all give the register one-step plan's gradient bit for bit."""
+    P = problem(nt=40)
+    ok = oracle_kw(P)
+    d_obs, _, _ = oracle.forward(P["shape"], P["h"], P["so"], P["dt"], P["nt"], P["m_true"].astype(np.float64),
+                                 src_xyz=P["src"], wavelet=P["wav"], rec_xyz=P["rec"], **ok)
+    dobs_t = torch.from_numpy(d_obs.astype(np.float32)).cuda()
+    ref = plan_for(W, P, P["m0"], tiling=(1, 16, 64, 34))
+    J_ref, g_ref = ref.gradient(dobs_t, checkpoint_every=9)
+    g_ref = g_ref.clone()
+    rec_a = ref.adjoint(dobs_t).clone()
+    ref.close()
+    plan = plan_for(W, P, P["m0"], tiling=tiling)
+    J, g = plan.gradient(dobs_t, checkpoint_every=9)
+    assert J == J_ref
+    assert torch.equal(g, g_ref)
+    assert torch.equal(plan.adjoint(dobs_t), rec_a)
+    plan.close()
