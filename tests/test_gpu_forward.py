@@ -222,11 +222,11 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(W, oracle):
 
 
 @pytest.mark.parametrize("so", [8, 16])
-def test_dense_receiver_surface_capture_mode(W, oracle, so):
-    """64 x 64 surface receivers at 25 m (all taps in the first z quad): the
-    capture path (quads stored whole, traces gathered per pass) gives the
-    same traces bit for bit as the per-tap path (forced by one extra receiver
-    deeper down), across one-step and tiled passes, and matches the oracle."""
+def test_dense_receiver_surface_gather(W, oracle, so):
+    """64 x 64 surface receivers at 25 m (all taps in the first z quad): with
+    one-step passes the traces are gathered from the field after each pass;
+    they equal, bit for bit, the per-tap path (forced by one extra receiver
+    deeper down, and used by the T = 2 pass), and match the oracle."""
     from paper_1707_02347_gb300 import inputs
 
     shape = (40, 37, 30)
