@@ -129,6 +129,17 @@ wave_status wave_set_receivers(wave_plan_t plan, int nrec, const double* xyz);
  * schedule the tile-legality scheduler does not accept (WAVE_ERR_ARG). */
 wave_status wave_set_tiling(wave_plan_t plan, const wave_tiling* tiling);
 
+/* wave_autotune with its result cached by key: the device (name and SM
+ * count), the grid, the space order, T_only and the set of compiled kernel
+ * variants.  A key seen before in this process applies the stored tiling
+ * without timing anything; with the environment variable
+ * WAVE_AUTOTUNE_CACHE=<path> results are also appended to that text file
+ * ("key T by bz xc unroll" per line, the last line of a key wins) and looked
+ * up there, so they persist across processes.  *from_cache (may be NULL) is
+ * set to 1 when the tiling came from the cache.  Errors as wave_autotune;
+ * an unreadable or unwritable file only disables the file. */
+wave_status wave_autotune_cached(wave_plan_t plan, int passes, int T_only, int* from_cache);
+
 /* The tiling the forward passes use now (after defaults / autotuning). */
 wave_status wave_get_tiling(wave_plan_t plan, wave_tiling* tiling);
 

@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
                                                  ctypes.c_int]),
             "wave_skewed_order_legal": (ctypes.c_int, [ctypes.c_int] * 6),
             "wave_batch_create": (st, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]),
+            "wave_autotune_cached": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "wave_batch_forward": (st, [_VP, ctypes.POINTER(_VP), _VP]),
             "wave_batch_gradient": (st, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _DP, ctypes.c_int, _VP]),
             "wave_batch_destroy": (st, [_VP]),
@@ -260,6 +261,13 @@ class WavePlan:
         n = ctypes.c_int(0)
         _check(self._lib.wave_autotune(self._h, int(passes), int(T_only), cands, ms, cap, ctypes.byref(n)))
         return [(cands[i].as_tuple(), ms[i]) for i in range(min(n.value, cap))]
+
+    def autotune_cached(self, passes=3, T_only=0):
+        """Autotune through the result cache (see wave_autotune_cached):
+        returns (tiling, from_cache)."""
+        hit = ctypes.c_int(0)
+        _check(self._lib.wave_autotune_cached(self._h, int(passes), int(T_only), ctypes.byref(hit)))
+        return self.get_tiling(), bool(hit.value)
 
     def forward(self, u_init=None, want_final=False, rec_out=None, u_final=None):
         """Run nt steps; returns (rec [nt, nrec], u_final [2, nx, ny, nz] or None)."""

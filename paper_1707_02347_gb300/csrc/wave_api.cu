@@ -809,6 +809,97 @@ extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave
     return apply_tiling(p, best_t);
 }
 
+namespace {
+
+// Autotuning results by key: device, grid, space order, T restriction and the
+// set of compiled kernel variants (a different build never reuses an entry).
+// Kept for the process; with WAVE_AUTOTUNE_CACHE=<path> also appended to, and
+// looked up in, that text file (one "key T by bz xc variant" line per result,
+// the last line of a key wins).
+std::mutex g_tune_mu;
+std::map<std::string, wave_tiling> g_tune;
+
+std::string tune_key(wave_plan_t p, int T_only)
+{
+    cudaDeviceProp prop;
+    std::string dev = cudaGetDeviceProperties(&prop, p->dev) == cudaSuccess ? prop.name : "device";
+    for (auto& c : dev)
+        if (c == ' ' || c == '|') c = '_';
+    int n = 0;
+    const PassShape* s = pass_shapes(&n);
+    unsigned long long h = 1469598103934665603ull;  // FNV-1a over the compiled variants
+    for (int i = 0; i < n; ++i)
+        for (int v : {s[i].R, s[i].T, s[i].qz, s[i].ry, s[i].unroll}) {
+            h ^= static_cast<unsigned long long>(v);
+            h *= 1099511628211ull;
+        }
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s|sm%d|%dx%dx%d|so%d|T%d|v%016llx", dev.c_str(), p->sm_count, p->n[0], p->n[1],
+                  p->n[2], p->so, T_only, h);
+    return buf;
+}
+
+bool tune_lookup(const std::string& key, wave_tiling* t)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+        *t = it->second;
+        return true;
+    }
+    const char* path = std::getenv("WAVE_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    bool found = false;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        char k[300];
+        wave_tiling r{};
+        if (std::sscanf(line, "%299s %d %d %d %d %d", k, &r.T, &r.by, &r.bz, &r.xc, &r.unroll) == 6 && key == k) {
+            *t = r;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    if (found) g_tune[key] = *t;
+    return found;
+}
+
+void tune_store(const std::string& key, const wave_tiling& t)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = t;
+    const char* path = std::getenv("WAVE_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), t.T, t.by, t.bz, t.xc, t.unroll);
+        std::fclose(f);
+    }
+}
+
+}  // namespace
+
+extern "C" wave_status wave_autotune_cached(wave_plan_t p, int passes, int T_only, int* from_cache)
+{
+    if (!p || passes < 1) return fail(WAVE_ERR_ARG, "wave_autotune_cached: bad argument");
+    if (from_cache) *from_cache = 0;
+    DeviceGuard g(p->dev);
+    const std::string key = tune_key(p, T_only);
+    wave_tiling t{};
+    PassGeom geom;
+    if (tune_lookup(key, &t) && make_geom(p->n, p->R, t, &geom, nullptr)) {
+        wave_status s = apply_tiling(p, t);
+        if (s) return s;
+        if (from_cache) *from_cache = 1;
+        return WAVE_OK;
+    }
+    wave_status s = wave_autotune(p, passes, T_only, nullptr, nullptr, 0, nullptr);
+    if (s) return s;
+    tune_store(key, p->tiling);
+    return WAVE_OK;
+}
+
 extern "C" wave_status wave_forward(wave_plan_t p, const float* u_init, float* rec_out, float* u_final)
 {
     if (!p) return fail(WAVE_ERR_ARG, "wave_forward: null plan");

@@ -287,3 +287,49 @@ def test_autotune_then_forward(W, oracle, so):
     assert np.array_equal(rec.cpu().numpy(), ref_rec)
     assert np.array_equal(uf.cpu().numpy(), ref_u)
     plan.close()
+
+
+def test_autotune_cache(W, tmp_path, monkeypatch):
+    """wave_autotune_cached: the first plan of a key times the candidates, a
+    second plan of the same key takes the stored tiling without timing, and
+    with WAVE_AUTOTUNE_CACHE the result persists to a fresh process."""
+    import os
+    import subprocess
+    import sys
+
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("WAVE_AUTOTUNE_CACHE", str(path))
+    script = """
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+import paper_1707_02347_gb300 as W
+from paper_1707_02347_gb300 import inputs
+w = inputs.layered_forward((40, 44, 36), 8, 9, seed=5, f=25.0, h=10.0, sponge_width=4)
+m = torch.from_numpy(np.ascontiguousarray(w.m)).cuda()
+p = W.WavePlan(w.shape, w.spacing, 8, w.dt, w.nt, m, sponge_width=w.sponge_width, vmax=w.vmax)
+t, hit = p.autotune_cached(passes=1)
+print(int(hit), *t)
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+    def run_here():
+        from paper_1707_02347_gb300 import inputs
+
+        w = inputs.layered_forward((40, 44, 36), 8, 9, seed=5, f=25.0, h=10.0, sponge_width=4)
+        m = torch.from_numpy(np.ascontiguousarray(w.m)).cuda()
+        p = W.WavePlan(w.shape, w.spacing, 8, w.dt, w.nt, m, sponge_width=w.sponge_width, vmax=w.vmax)
+        t, hit = p.autotune_cached(passes=1)
+        p.close()
+        return t, hit
+
+    t1, hit1 = run_here()
+    assert not hit1
+    t2, hit2 = run_here()
+    assert hit2 and t2 == t1
+    lines = path.read_text().splitlines()
+    assert any(line.split()[1:] == [str(v) for v in t1] for line in lines)
+    out = subprocess.run([sys.executable, "-c", script.format(root=root)], capture_output=True, text=True,
+                         env=dict(os.environ), timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    fields = out.stdout.split()
+    assert fields[0] == "1" and tuple(int(v) for v in fields[1:]) == tuple(t1)
