@@ -57,10 +57,15 @@ typedef struct wave_plan_s* wave_plan_t;
  *   by     : output tile extent along y (points);
  *   bz     : output tile extent along z (points, multiple of 4);
  *   xc     : extent along x of the slab one thread block streams through;
- *   unroll : where the per-column queue of planes along x lives and how it
- *            advances: 0 = registers, moved in a compact loop; 1 = registers,
- *            loop unrolled over the queue length; 2 = tensor memory (a ring
- *            per warp, read back with tcgen05.ld; no register queue).
+ *   unroll : the kernel variant: where the per-column queue of planes along
+ *            x lives and how the pass is organised.  0 = registers, moved in
+ *            a compact loop; 1 = registers, loop unrolled over the queue
+ *            length; 2 = tensor memory (a ring per warp, read back with
+ *            tcgen05.ld; no register queue); 4 = skewed wavefront tiling in y
+ *            (T = 2, tensor memory); 5 and 6 = warp-specialised pass (a
+ *            producer warp issues the TMA copies, no block-wide barrier per
+ *            plane, tensor memory), 1 (5) or 2 (6) rows per thread.
+ *            Every variant computes bit-identical fields.
  * (T, by, bz, unroll) must name a compiled kernel variant (wave_tiling_check).
  * Fields T, by, bz, xc of 0 = let the library choose. */
 typedef struct {

@@ -331,22 +331,28 @@ __device__ __forceinline__ void pair2(float2& Ll, float2& Lh, float2 coef, const
     }
 }
 
-// Ly and Lz of the quad with centre c.  plane: shared-memory plane holding u
-// of this step's input level at the current x with a halo of r rows and ZH
-// columns; pos: the quad's own index.
-template <int R>
-__device__ __forceinline__ void laplacian_yz(const float* plane, int pos, int pitch, const float4& c,
-                                             const PassArgs& a, float2& yl, float2& yh, float2& zl, float2& zh)
+// Ly of the quad with centre c (the centre term and the y pairs);
+// yq(k) is the quad k rows away, k = -r .. r, called with compile-time k.
+template <int R, class YQ>
+__device__ __forceinline__ void laplacian_y(const float4& c, const YQ& yq, const PassArgs& a, float2& yl, float2& yh)
 {
-    constexpr int NQ = ((R + 3) & ~3) / 4;
     yl = __fmul2_rn(a.c0, lo2(c));
     yh = __fmul2_rn(a.c0, hi2(c));
-#pragma unroll
-    for (int k = 1; k <= R; ++k) {
-        const float4 m = lds4(plane + pos - k * pitch);
-        const float4 p = lds4(plane + pos + k * pitch);
-        pair2(yl, yh, a.cy[k - 1], m, p, c, k == 1, false);
-    }
+    static_for<R>([&](auto kc) {
+        constexpr int k = decltype(kc)::value + 1;
+        pair2(yl, yh, a.cy[k - 1], yq(std::integral_constant<int, -k>{}), yq(std::integral_constant<int, k>{}), c,
+              k == 1, false);
+    });
+}
+
+// Lz of the quad with centre c.  plane: shared-memory plane holding u of
+// this step's input level at the current x with a halo of ZH columns; pos:
+// the quad's own index.
+template <int R>
+__device__ __forceinline__ void laplacian_z(const float* plane, int pos, const float4& c, const PassArgs& a,
+                                            float2& zl, float2& zh)
+{
+    constexpr int NQ = ((R + 3) & ~3) / 4;
     // z window: the centre quad and NQ quads on each side, one float per point
     float w[4 * (2 * NQ + 1)];
 #pragma unroll
@@ -382,6 +388,17 @@ __device__ __forceinline__ void laplacian_yz(const float* plane, int pos, int pi
             pair2(zl, zh, a.cz[k - 1], m, p, c, false, false);
         }
     });
+}
+
+// Ly and Lz of the quad with centre c.  plane: shared-memory plane holding u
+// of this step's input level at the current x with a halo of r rows and ZH
+// columns; pos: the quad's own index.
+template <int R>
+__device__ __forceinline__ void laplacian_yz(const float* plane, int pos, int pitch, const float4& c,
+                                             const PassArgs& a, float2& yl, float2& yh, float2& zl, float2& zh)
+{
+    laplacian_y<R>(c, [&](auto kc) { return lds4(plane + pos + decltype(kc)::value * pitch); }, a, yl, yh);
+    laplacian_z<R>(plane, pos, c, a, zl, zh);
 }
 
 // Lx of the quad with centre c; xq(j) is the quad's u at logical plane j of

@@ -2,12 +2,16 @@
 // Each entry is one (T, z quads per row, thread rows, queue storage) variant the
 // autotuner can pick; queue storage 0/1 = registers (moved / rotated), 2 = tensor memory;
 // variant 4 = two-step pass with skewed wavefront tiling in y (tensor-memory queues).
+#include "wave_lean.cuh"
 #include "wave_skew.cuh"
 
 namespace wave {
 
 #define WAVE_SHAPE(T, QZ, RY, QM) \
     {4, T, QZ, RY, QM, detail::smem_bytes<4, T, QZ, RY>(), &detail::launch_impl<4, T, QZ, RY, QM>}
+// variants 5 and 6: warp-specialised pass, NY = 1 or 2 rows per thread, x queues in tensor memory
+#define WAVE_LEAN(T, QZ, RY, NY) \
+    {4, T, QZ, RY, 4 + NY, detail::lean_smem_bytes<4, T, QZ, RY, NY>(), &detail::launch_lean<4, T, QZ, RY, NY>}
 // variant 4: skewed wavefront tiling in y, T = 2, x queues in tensor memory
 #define WAVE_SKEW(QZ, RY) {4, 2, QZ, RY, 4, detail::skew_smem_bytes<4, QZ, RY>(), &detail::launch_skew<4, QZ, RY>}
 
@@ -36,6 +40,7 @@ const PassShape* pass_shapes_r4(int* n)
         WAVE_SHAPE(3, 8, 32, 2),
         WAVE_SKEW(16, 32),
         WAVE_SKEW(8, 64),
+        WAVE_LEAN(2, 16, 32, 1),
     };
     *n = static_cast<int>(sizeof(shapes) / sizeof(shapes[0]));
     return shapes;
