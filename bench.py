@@ -126,12 +126,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(load), "power_w_max": max(pw) if pw else None}
 
 
-def kernel_traffic(T, so=8):
-    """dram bytes per grid point per launch of the pass kernel from the
-    committed ncu summary of this space order, only if it was taken on the
-    current kernel source."""
-    src = os.path.join(ROOT, "paper_1707_02347_gb300", "csrc", "wave_pass.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+# source files of each pass kernel variant: overlapped halos (0-2), skewed
+# wavefront (4), warp-specialised (5, 6); the kernel files include wave_pass.cuh
+def kernel_sources(variant):
+    extra = {4: ("wave_skew.cuh",), 5: ("wave_lean.cuh",), 6: ("wave_lean.cuh",)}.get(variant, ())
+    return ("wave_pass.cuh",) + extra
+
+
+def kernel_name(so, T, variant):
+    base = {4: "skew_kernel", 5: "lean_kernel", 6: "lean_kernel"}.get(variant, "pass_kernel")
+    return "%s<%d,%d> (SO%d, T=%d, variant %d)" % (base, so // 2, T, so, T, variant)
+
+
+def kernel_traffic(T, so=8, variant=2):
+    """dram bytes per grid point per launch of the pass kernel (T, variant)
+    from the committed ncu summary of this space order, only if it was taken
+    on the current kernel sources."""
+    sha = hashlib.sha256()
+    for f in kernel_sources(variant):
+        sha.update(open(os.path.join(ROOT, "paper_1707_02347_gb300", "csrc", f), "rb").read())
+    h = sha.hexdigest()[:16]
     name = {8: "tiled_pass_so8_512.md", 16: "tiled_pass_so16_768.md"}.get(so)
     if name is None:
         return None, h
@@ -140,7 +154,7 @@ def kernel_traffic(T, so=8):
         return None, h
     txt = open(path).read()
     m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    m_t = re.search(r"dram_bytes_per_point_T%d:\s*([0-9.eE+-]+)" % T, txt)
+    m_t = re.search(r"dram_bytes_per_point_T%d_v%d:\s*([0-9.eE+-]+)" % (T, variant), txt)
     if not m_h or not m_t or m_h.group(1) != h:
         return None, h
     return float(m_t.group(1)), h
@@ -478,10 +492,11 @@ def main():
     bytes_per_launch = 20.0 * npts  # read u, v, kappa; write u, v (once per pass)
     avg_launch_s = (pass_ms / max(nl, 1)) * 1e-3
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    traffic_pp, src_hash = kernel_traffic(T, so)
+    variant = best[4] if len(best) > 4 else 0
+    traffic_pp, src_hash = kernel_traffic(T, so, variant)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic_pp * npts if traffic_pp is not None else None,
-            "kernel": "pass_kernel<%d,%d> (SO%d, T=%d)" % (so // 2, T, so, T), "peak_kind": peak_kind,
+            "kernel": kernel_name(so, T, variant), "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
             "launches_timed": nl, "kernel_source_sha256_16": src_hash}
     flops_pp = 9 * (so // 2) + 5  # per point-step: 3 axes x r pairs x (add + fma), centre, update

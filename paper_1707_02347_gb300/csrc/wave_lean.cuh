@@ -61,6 +61,23 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting warp sleeps until the phase
+// completes (or the hint runs out) instead of spinning on issue slots that
+// the working warps of the SM need.
+constexpr uint32_t kSuspendHintNs = 20000;
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "n"(kSuspendHintNs)
+        : "memory");
+    return ok != 0;
+}
+
 // mbar_wait that also gives up as soon as another warp has set the block's
 // abort word.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_word)
@@ -68,8 +85,8 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
-        for (int k = 0; k < 64; ++k)
-            if (mbar_try(bar, parity)) return true;
+        for (int k = 0; k < 8; ++k)
+            if (mbar_try_sleep(bar, parity)) return true;
         if (*abort_word) return false;
         if (global_ns() - t0 > kWaitLimitNs) return false;
     }
