@@ -167,11 +167,12 @@ def test_fwi_autograd_function(W, oracle):
     plan.close()
 
 
-@pytest.mark.parametrize("tiling", [(2, 28, 56, 34, 4), (2, 24, 56, 34, 2), (1, 8, 64, 34, 2)])
+@pytest.mark.parametrize("tiling", [(2, 28, 56, 34, 4), (2, 24, 56, 34, 2), (1, 8, 64, 34, 2), (2, 24, 56, 34, 5)])
 def test_gradient_independent_of_pass_variant(W, oracle, tiling):
     """The gradient runs its forward and adjoint sweeps with the plan's
-    tiling: the skewed wavefront variant, the tensor-memory T = 2 pass and the
-    one-step pass all give the register one-step plan's gradient bit for bit."""
+    tiling: the skewed wavefront variant, the tensor-memory T = 2 pass, the
+    warp-specialised T = 2 pass and the one-step pass all give the register
+    one-step plan's gradient bit for bit."""
     P = problem(nt=40)
     ok = oracle_kw(P)
     d_obs, _, _ = oracle.forward(P["shape"], P["h"], P["so"], P["dt"], P["nt"], P["m_true"].astype(np.float64),
