@@ -140,6 +140,24 @@ def test_tiling_check_skewed_variant(W, so, tiling, ok):
     assert W.tiling_check((512, 512, 512), so, tiling) == ok
 
 
+@pytest.mark.parametrize("so,tiling,ok", [
+    # warp-specialised variants: 5 = one row per thread, 6 = two rows per thread
+    # (a compute thread per 2 rows of a z quad); compiled for the listed shapes only
+    (8, (2, 24, 56, 128, 5), True), (8, (2, 24, 56, 128, 6), False), (8, (1, 16, 64, 128, 5), False),
+    (4, (2, 28, 56, 128, 5), True), (4, (3, 24, 56, 128, 5), True), (4, (2, 28, 56, 128, 6), False),
+    (16, (1, 64, 32, 128, 6), True), (16, (1, 32, 64, 256, 6), True), (16, (1, 32, 64, 256, 5), False),
+])
+def test_tiling_check_warp_specialised_variants(W, so, tiling, ok):
+    assert W.tiling_check((512, 512, 512), so, tiling) == ok
+
+
+@pytest.mark.parametrize("so,tiling", [(8, (2, 24, 56, 16, 5)), (4, (3, 24, 56, 9, 5)), (16, (1, 64, 32, 8, 6))])
+def test_warp_specialised_schedule_is_legal(W, so, tiling):
+    # same tiles and skew as the overlapped pass; only the synchronisation differs
+    ok, msg = W.schedule_verify((40, 36, 44), so, tiling)
+    assert ok, msg
+
+
 def test_schedule_verifier_declines_skewed_variant(W):
     # the brute-force verifier models independent (overlapped) tiles only; the
     # skewed variant is checked bit for bit against the one-step kernel on the GPU
