@@ -138,8 +138,9 @@ def kernel_name(so, T, variant):
     return "%s<%d,%d> (SO%d, T=%d, variant %d)" % (base, so // 2, T, so, T, variant)
 
 
-def kernel_traffic(T, so=8, variant=2):
-    """dram bytes per grid point per launch of the pass kernel (T, variant)
+def kernel_traffic(T, so=8, variant=2, key="dram_bytes_per_point"):
+    """dram bytes (or, with key="smem_wavefronts_per_point", shared-memory
+    wavefronts) per grid point per launch of the pass kernel (T, variant)
     from the committed ncu summary of this space order, only if it was taken
     on the current kernel sources."""
     sha = hashlib.sha256()
@@ -154,7 +155,7 @@ def kernel_traffic(T, so=8, variant=2):
         return None, h
     txt = open(path).read()
     m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    m_t = re.search(r"dram_bytes_per_point_T%d_v%d:\s*([0-9.eE+-]+)" % (T, variant), txt)
+    m_t = re.search(r"%s_T%d_v%d:\s*([0-9.eE+-]+)" % (key, T, variant), txt)
     if not m_h or not m_t or m_h.group(1) != h:
         return None, h
     return float(m_t.group(1)), h
@@ -480,11 +481,15 @@ def main():
             T2 = tiled_tiling[0]
             hbm_pk = peaks()[0]
             launch_s = pms2 / max(nl2, 1) * 1e-3
+            wf2, _ = kernel_traffic(T2, so, tiled_tiling[4] if len(tiled_tiling) > 4 else 0,
+                                    "smem_wavefronts_per_point")
             untiled["best_time_tiled"] = {
                 "value": v2, "unit": "GPt/s", "ms_per_step": ms2 / args.steps, "tiling": list(tiled_tiling),
                 "speedup_over_untiled": v2 / v1, "algorithmic_bytes_per_point_step": 20.0 / T2,
                 "pass_avg_launch_ms": launch_s * 1e3,
-                "hbm_frac": 20.0 * npts / launch_s / 1e9 / hbm_pk}
+                "hbm_frac": 20.0 * npts / launch_s / 1e9 / hbm_pk,
+                "smem_frac": (wf2 * npts * 128 / launch_s / 1e9 / (152 * 128 * peaks()[1] * 1e6 / 1e9)
+                              if wf2 is not None else None)}
     clk.stop()
 
     hbm, smmax, peak_kind = peaks()
@@ -501,6 +506,16 @@ def main():
             "launches_timed": nl, "kernel_source_sha256_16": src_hash}
     flops_pp = 9 * (so // 2) + 5  # per point-step: 3 axes x r pairs x (add + fma), centre, update
     fp32_peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
+    # shared memory: one 128-byte wavefront per SM and clock
+    wf_pp, _ = kernel_traffic(T, so, variant, "smem_wavefronts_per_point")
+    smem_peak = 152 * 128 * smmax * 1e6 / 1e9
+    roof_smem = None
+    if wf_pp is not None:
+        smem_ach = wf_pp * npts * 128 / avg_launch_s / 1e9
+        roof_smem = {"bound": "smem", "achieved": smem_ach, "peak": smem_peak, "unit": "GB/s",
+                     "frac": smem_ach / smem_peak, "wavefronts_per_point": wf_pp,
+                     "note": "shared-memory load/store wavefronts of one launch (ncu, 128 B each) over the "
+                             "measured launch time, vs one wavefront per SM per clock at max clock"}
     roof_alu = {"bound": "alu", "achieved": flops_pp * pass_pts / (pass_ms * 1e-3) / 1e12, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": flops_pp * pass_pts / (pass_ms * 1e-3) / 1e12 / fp32_peak,
                 "flops_per_point_step": flops_pp,
@@ -539,9 +554,9 @@ def main():
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": workload_name, "grid": list(w.shape), "so": so, "nt": w.nt, "tiling": list(best),
-                          "dt_ms": w.dt, "l2": "inputs larger than L2 (each field 537 MB > 129 MB)",
+                          "dt_ms": w.dt, "l2": "inputs larger than L2 (each field %.0f MB > 129 MB)" % (npts * 4 / 1e6),
                           "parallelism": "replicas" if world > 1 else "single GPU"},
-               "untiled": untiled, "roofline": roof, "roofline_alu": roof_alu,
+               "untiled": untiled, "roofline": roof, "roofline_alu": roof_alu, "roofline_smem": roof_smem,
                "hbm_bound_16B_untiled_gpts": hbm / 16.0,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
                "autotune": [[list(t), ms_] for t, ms_ in sorted(tuned, key=lambda c: c[1])[:8]]}
