@@ -126,6 +126,28 @@ def test_layered_so8_long_run_vs_oracle(W, oracle):
     assert rel_l2(rec, rec_o) <= TOL
 
 
+@pytest.mark.parametrize("so,shape,tilings", [
+    # SO16: the two-row warp-specialised one-step pass the SO16 bench picks, and the one-row pass
+    (16, (56, 52, 48), [(1, 64, 32, 40, 6), (1, 32, 64, 56, 2)]),
+    # SO4: the three-step warp-specialised pass and the one-step pass
+    (4, (64, 60, 56), [(3, 24, 56, 40, 5), (1, 16, 64, 64, 0)]),
+])
+def test_layered_long_run_vs_oracle(W, oracle, so, shape, tilings):
+    """400 steps (the accumulated float32 rounding of a long run) against the
+    FP64 oracle, through the sponge and the free surface; the variants agree
+    bit for bit."""
+    w = small_layered(shape, so, 400, seed=30 + so, f=20.0, sponge=8)
+    rec_o, up_o, uc_o = run_oracle(oracle, w)
+    rec, uf = run_gpu(W, w, tilings[0])
+    assert rel_l2(uf[1], uc_o) <= TOL
+    assert rel_l2(uf[0], up_o) <= TOL
+    assert rel_l2(rec, rec_o) <= TOL
+    for t in tilings[1:]:
+        rec2, uf2 = run_gpu(W, w, t)
+        assert np.array_equal(rec2, rec), t
+        assert np.array_equal(uf2, uf), t
+
+
 def test_gaussian_initial_field_source_free(W, oracle):
     """Section "Functional Correctness": source removed, u initialised with a
     3D Gaussian (sigma 0.4 on [-1, 1]^3); tiled vs untiled and vs the oracle."""
