@@ -16,6 +16,7 @@ cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -221,9 +222,24 @@ def cpu_baseline(w):
     k = int(max(1, min(20, 12.0 / max(t1, 1e-3))))
     tk = run(k)
     pts = float(np.prod(w.shape)) * k
-    return {"value": pts / tk / 1e9, "unit": "GPt/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d time steps of the full %s SO8 workload (FP64, OpenMP over x), %.1f s" %
-                      (k, "x".join(str(s) for s in w.shape), tk)}
+    grid = "x".join(str(s) for s in w.shape)
+    out = {"value": pts / tk / 1e9, "unit": "GPt/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "%d time steps of the full %s SO%d workload (FP64, OpenMP over x), %.1f s" %
+                     (k, grid, w.so, tk)}
+    # the same oracle on one core: one time step of the full grid
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+        gomp.omp_set_num_threads(1)
+        try:
+            t1c = run(1)
+        finally:
+            gomp.omp_set_num_threads(os.cpu_count())
+        out["single_core"] = {"value": float(np.prod(w.shape)) / t1c / 1e9, "unit": "GPt/s", "cores": 1,
+                              "sample": "1 time step of the full %s SO%d workload on one thread, %.1f s" %
+                                        (grid, w.so, t1c)}
+    except OSError:
+        out["single_core"] = None
+    return out
 
 
 def run_batched(args, W, inputs, dev, world, rank, dist):
