@@ -162,7 +162,7 @@ def test_gaussian_initial_field_source_free(W, oracle):
     _, ref = run_gpu(W, w, (1, 8, 64, 44), u_init=u0)
     _, up_o, uc_o = run_oracle(oracle, w, u_init=u0)
     assert rel_l2(ref[1], uc_o) <= TOL
-    for t in [(2, 16, 56, 44), (3, 16, 16, 20)]:
+    for t in [(2, 16, 56, 44), (3, 16, 16, 20), (2, 24, 56, 44, 5)]:
         _, uf = run_gpu(W, w, t, u_init=u0)
         assert np.array_equal(uf, ref), t
 
@@ -173,18 +173,24 @@ def test_edge_cases(W, oracle):
     # minimum grid (so + 1 per axis), nz not a multiple of 4
     w = small_layered((9, 9, 9), 8, 7, seed=2, nrec=3, sponge=2)
     rec_o, up_o, uc_o = run_oracle(oracle, w)
-    for t in [(1, 8, 64, 9), (2, 8, 56, 5), (3, 16, 16, 9)]:
+    for t in [(1, 8, 64, 9), (2, 8, 56, 5), (3, 16, 16, 9), (2, 24, 56, 5, 5)]:
         rec, uf = run_gpu(W, w, t)
         assert rel_l2(uf[1], uc_o) <= TOL and rel_l2(rec, rec_o) <= TOL, t
+    # minimum SO16 grid, the two-row warp-specialised pass (tile larger than the grid)
+    w = small_layered((17, 17, 17), 16, 5, seed=3, nrec=3, sponge=2)
+    rec_o, _, uc_o = run_oracle(oracle, w)
+    rec, uf = run_gpu(W, w, (1, 64, 32, 17, 6))
+    assert rel_l2(uf[1], uc_o) <= TOL and rel_l2(rec, rec_o) <= TOL
     # nt = 0: the initial fields come back (u^0 exactly, u^{-1} through one
     # rounding of the stored increment u^0 - u^{-1}) and there are no traces
     w0 = small_layered((20, 18, 17), 4, 0, seed=4)
     rng = np.random.default_rng(0)
     u0 = rng.standard_normal((2,) + w0.shape).astype(np.float32)
-    rec, uf = run_gpu(W, w0, (2, 12, 56, 20), u_init=u0)
-    assert rec.shape == (0, w0.rec_xyz.shape[0])
-    assert np.array_equal(uf[1], u0[1])
-    np.testing.assert_allclose(uf[0], u0[0], rtol=0, atol=2.5e-7 * np.abs(u0).max())
+    for t in [(2, 12, 56, 20), (2, 28, 56, 20, 5)]:
+        rec, uf = run_gpu(W, w0, t, u_init=u0)
+        assert rec.shape == (0, w0.rec_xyz.shape[0])
+        assert np.array_equal(uf[1], u0[1])
+        np.testing.assert_allclose(uf[0], u0[0], rtol=0, atol=2.5e-7 * np.abs(u0).max())
     # nt not a multiple of T; two sources on the same grid point
     w = small_layered((30, 28, 26), 4, 11, seed=7)
     w.src_xyz = np.vstack([w.src_xyz, w.src_xyz[:1]])
@@ -193,9 +199,11 @@ def test_edge_cases(W, oracle):
     r1, u1 = run_gpu(W, w, (1, 16, 64, 30))
     r3, u3 = run_gpu(W, w, (3, 24, 24, 30))
     r4, u4 = run_gpu(W, w, (4, 20, 16, 30))
+    r5, u5 = run_gpu(W, w, (3, 24, 56, 30, 5))
     assert rel_l2(u1[1], uc_o) <= TOL and rel_l2(r1, rec_o) <= TOL
     assert np.array_equal(u1, u3) and np.array_equal(r1, r3)
     assert np.array_equal(u1, u4) and np.array_equal(r1, r4)
+    assert np.array_equal(u1, u5) and np.array_equal(r1, r5)
 
 
 def test_invalid_arguments(W):
