@@ -110,3 +110,70 @@ def test_batched_gradients_match_single_plans(oracle):
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_full_size_batched_shots(oracle):
+    """Four shots of the 24-shot workload at their full sizes (the same draws
+    of seed 5: grids U[128, 320] x U[128, 320] x U[128, 256], SO 4/8, 600 steps,
+    Ricker 8-15 Hz, 64 receivers at 20 m), each with the tiling the autotuner
+    picks for it (variants 0, 2 and 5, T = 1 and 2): the batched forward and
+    the batched gradient (checkpoints every 40 steps) equal the single plans
+    bit for bit, and the smallest shot's traces match the FP64 oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1707_02347_gb300 as W
+    from paper_1707_02347_gb300 import inputs
+
+    W.load()
+    dev = torch.device("cuda")
+    nt = 600
+    rng = np.random.default_rng(5)
+    draws = []
+    for s in range(24):
+        shape = (int(rng.integers(128, 321)), int(rng.integers(128, 321)), int(rng.integers(128, 257)))
+        draws.append((shape, 4 if s % 2 == 0 else 8, float(rng.uniform(8.0, 15.0))))
+    picked = {0: (2, 28, 56, 64, 5), 2: (2, 12, 56, 64, 0), 3: (2, 24, 24, 64, 0), 21: (1, 8, 64, 64, 2)}
+    plans, works, m_true = [], [], []
+    for s, tiling in picked.items():
+        shape, so, f = draws[s]
+        w = inputs.layered_forward(shape, so, nt, seed=500 + s, f=f, h=10.0, sponge_width=10, nrec_line=64)
+        m = torch.from_numpy(np.ascontiguousarray(w.m)).to(dev)
+        p = W.WavePlan(w.shape, w.spacing, so, w.dt, nt, m, sponge_width=w.sponge_width, vmax=w.vmax, tiling=tiling)
+        p.set_sources(w.src_xyz, torch.from_numpy(w.wavelet.astype(np.float32)).to(dev))
+        p.set_receivers(w.rec_xyz)
+        plans.append(p)
+        works.append(w)
+        m_true.append(m)
+    single = [p.forward()[0].clone() for p in plans]
+    batch = W.WaveBatch(plans)
+    recs = batch.forward()
+    torch.cuda.synchronize()
+    for r, r1 in zip(recs, single):
+        assert torch.equal(r, r1)
+    # the smallest shot (206 x 128 x 134, SO8) against the oracle
+    k = list(picked).index(3)
+    w = works[k]
+    rec_o, _, _ = oracle.forward(w.shape, w.spacing, w.so, w.dt, nt, w.m.astype(np.float64), src_xyz=w.src_xyz,
+                                 wavelet=w.wavelet.astype(np.float32).astype(np.float64), rec_xyz=w.rec_xyz,
+                                 sponge_width=w.sponge_width, sponge_faces=w.sponge_faces, vmax=w.vmax)
+    got = recs[k].cpu().numpy().astype(np.float64)
+    assert np.abs(rec_o).max() > 0.0
+    assert np.linalg.norm(got - rec_o) <= 1e-5 * np.linalg.norm(rec_o)
+    # gradients on a start model 3 % slower
+    d_obs = [r.clone() for r in recs]
+    for p, m in zip(plans, m_true):
+        p.set_model(m * 1.03 ** 2)
+    single_g = []
+    for p, d in zip(plans, d_obs):
+        J, g = p.gradient(d, checkpoint_every=40)
+        single_g.append((J, g.clone()))
+    mis, grads = batch.gradient(d_obs, checkpoint_every=40)
+    torch.cuda.synchronize()
+    for (J, g), j2, g2 in zip(single_g, mis, grads):
+        assert np.isfinite(J) and J > 0.0
+        assert j2 == J
+        assert torch.equal(g2, g)
+        assert bool(torch.isfinite(g2).all())
+    batch.close()
+    for p in plans:
+        p.close()
