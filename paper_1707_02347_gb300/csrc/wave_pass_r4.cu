@@ -1,7 +1,8 @@
 // wave_pass_r4.cu -- instantiations of the pass kernel for stencil radius 4 (SO 8).
 // Each entry is one (T, z quads per row, thread rows, queue storage) variant the
 // autotuner can pick; queue storage 0/1 = registers (moved / rotated), 2 = tensor memory;
-// variant 4 = two-step pass with skewed wavefront tiling in y (tensor-memory queues).
+// variant 4 = two-step pass with skewed wavefront tiling in y (tensor-memory queues);
+// variant 5 = warp-specialised pass with 1 row per thread (tensor-memory queues).
 #include "wave_lean.cuh"
 #include "wave_skew.cuh"
 
