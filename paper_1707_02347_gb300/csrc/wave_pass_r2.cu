@@ -43,6 +43,8 @@ const PassShape* pass_shapes_r2(int* n)
         WAVE_SKEW(16, 32),
         WAVE_LEAN(2, 16, 32, 1),
         WAVE_LEAN(3, 16, 32, 1),
+        WAVE_LEAN(1, 16, 8, 1),
+        WAVE_LEAN(1, 16, 16, 1),
     };
     *n = static_cast<int>(sizeof(shapes) / sizeof(shapes[0]));
     return shapes;

@@ -42,6 +42,8 @@ const PassShape* pass_shapes_r4(int* n)
         WAVE_SKEW(16, 32),
         WAVE_SKEW(8, 64),
         WAVE_LEAN(2, 16, 32, 1),
+        WAVE_LEAN(1, 16, 8, 1),
+        WAVE_LEAN(1, 16, 16, 1),
     };
     *n = static_cast<int>(sizeof(shapes) / sizeof(shapes[0]));
     return shapes;

@@ -94,12 +94,13 @@ def test_plain_forward_64_so4_vs_oracle(W, oracle):
     (4, (37, 34, 30), [(1, 16, 64, 11), (2, 28, 24, 9), (3, 24, 24, 40), (4, 12, 48, 13), (1, 16, 64, 37, 1),
                        (2, 12, 56, 30, 1), (3, 24, 24, 19, 1), (1, 16, 64, 37, 2), (2, 28, 56, 30, 2),
                        (3, 24, 56, 19, 2), (2, 20, 56, 20, 2), (4, 20, 16, 13, 2), (2, 30, 56, 30, 4),
-                       (2, 28, 56, 13, 5), (3, 24, 56, 19, 5)]),
+                       (2, 28, 56, 13, 5), (3, 24, 56, 19, 5), (1, 8, 64, 37, 5), (1, 16, 64, 11, 5)]),
     (8, (41, 35, 38), [(1, 32, 32, 40), (2, 24, 24, 10), (2, 16, 56, 41), (3, 16, 16, 17), (1, 32, 32, 41, 1),
                        (1, 16, 64, 23, 1), (2, 16, 56, 41, 1), (2, 24, 24, 29, 1), (3, 16, 16, 40, 1),
                        (1, 8, 64, 41, 2), (1, 16, 64, 23, 2), (2, 16, 56, 41, 2), (2, 24, 56, 29, 2),
                        (2, 56, 24, 17, 2), (3, 16, 16, 40, 2), (1, 32, 64, 41, 2), (2, 28, 56, 41, 4),
-                       (2, 60, 24, 13, 4), (2, 24, 56, 29, 5), (2, 24, 56, 17, 5)]),
+                       (2, 60, 24, 13, 4), (2, 24, 56, 29, 5), (2, 24, 56, 17, 5), (1, 8, 64, 41, 5),
+                       (1, 16, 64, 23, 5)]),
     (16, (36, 33, 34), [(1, 16, 64, 12), (2, 16, 16, 12), (2, 16, 16, 40), (1, 32, 32, 7), (1, 16, 64, 36, 1),
                         (2, 16, 16, 36, 1), (1, 8, 64, 36, 2), (1, 16, 64, 12, 2), (2, 16, 16, 36, 2),
                         (1, 32, 64, 36, 2), (1, 32, 64, 36, 6), (1, 64, 32, 12, 6)]),

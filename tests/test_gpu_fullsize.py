@@ -1,11 +1,12 @@
 """Parity at the full sizes, in the launch configurations the benchmark
-times: the 512^3 SO8 workload (T = 1 and T = 2 passes with the x queues in
-tensor memory) and the 768 x 768 x 384 SO16 workload with its 501 x 501
-receiver surface (the warp-specialised one-step pass with two rows per
-thread).
+times: the 512^3 SO8 workload (the warp-specialised one-step pass the
+autotuner picks, and the T = 2 pass with the x queues in tensor memory) and
+the 768 x 768 x 384 SO16 workload with its 501 x 501 receiver surface (the
+warp-specialised one-step pass with two rows per thread).
 
-The skewed wavefront and warp-specialised variants of the two-step pass, and
-the one-row SO16 pass, are checked against the same passes bit for bit.
+The other variants (the block-barrier one-step pass, the skewed wavefront
+and warp-specialised two-step passes, the one-row SO16 pass) are checked
+against the same passes bit for bit.
 
 The FP64 oracle cannot run the whole grid, so outputs are checked one by one:
 the GPU runs the workload for n1 steps and keeps the state (u^{n1-1}, u^{n1});
@@ -49,9 +50,9 @@ def state(oracle):
     _, uA = plan.forward(want_final=True)
     plan.close()
     out = {}
-    for T, tiling in ((1, (1, 8, 64, 64, 2)), (2, (2, 24, 56, 128, 2)), ("skew", (2, 28, 56, 128, 4)),
-                      ("lean", (2, 24, 56, 256, 5))):
-        nT = 2 if T in ("skew", "lean") else T
+    for T, tiling in ((1, (1, 8, 64, 64, 5)), ("T1v2", (1, 8, 64, 64, 2)), (2, (2, 24, 56, 128, 2)),
+                      ("skew", (2, 28, 56, 128, 4)), ("lean", (2, 24, 56, 256, 5))):
+        nT = 2 if T in (2, "skew", "lean") else 1
         p = W.WavePlan(w.shape, w.spacing, SO, w.dt, nT, m, sponge_width=w.sponge_width, vmax=w.vmax, tiling=tiling)
         p.set_sources(w.src_xyz, torch.from_numpy(wav[N1:N1 + nT].copy()).to(dev))
         _, uB = p.forward(u_init=uA, want_final=True)
@@ -129,6 +130,11 @@ def test_full_size_two_one_step_passes_equal_one_t2_pass(state):
     assert np.array_equal(out["T1x2"], out[2])
     assert np.array_equal(out["T1x2"], out["skew"])  # the skewed wavefront variant of the two-step pass
     assert np.array_equal(out["T1x2"], out["lean"])  # the warp-specialised two-step pass
+
+
+def test_full_size_one_step_variants_bit_identical(state):
+    _, _, out = state
+    assert np.array_equal(out[1], out["T1v2"])  # warp-specialised vs block-barrier one-step pass
 
 
 N1_16 = 100  # SO16 steps before the checked pass (the Ricker peaks near step 66)
