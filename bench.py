@@ -155,7 +155,7 @@ def kernel_traffic(T, so=8, variant=2, key="dram_bytes_per_point"):
     if not os.path.exists(path):
         return None, h
     txt = open(path).read()
-    m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_h = re.search(r"kernel_source_sha256_16_v%d:\s*([0-9a-f]+)" % variant, txt)
     m_t = re.search(r"%s_T%d_v%d:\s*([0-9.eE+-]+)" % (key, T, variant), txt)
     if not m_h or not m_t or m_h.group(1) != h:
         return None, h

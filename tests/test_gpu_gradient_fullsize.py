@@ -32,7 +32,7 @@ def test_full_size_gradient_fd_check_and_checkpoint_invariance():
     m0_h = inputs.slowness2(v0).astype(np.float32)
     m0 = torch.from_numpy(m0_h).to(dev)
     plan = W.WavePlan(w.shape, w.spacing, 8, w.dt, NT, m_true, sponge_width=w.sponge_width, vmax=w.vmax,
-                      tiling=(1, 8, 64, 64, 2))
+                      tiling=(1, 16, 64, 64, 5))
     plan.set_sources(w.src_xyz, torch.from_numpy(w.wavelet.astype(np.float32)).to(dev))
     plan.set_receivers(w.rec_xyz)
     d_obs, _ = plan.forward()
