@@ -143,7 +143,8 @@ def test_tiling_check_skewed_variant(W, so, tiling, ok):
 @pytest.mark.parametrize("so,tiling,ok", [
     # warp-specialised variants: 5 = one row per thread, 6 = two rows per thread
     # (a compute thread per 2 rows of a z quad); compiled for the listed shapes only
-    (8, (2, 24, 56, 128, 5), True), (8, (2, 24, 56, 128, 6), False), (8, (1, 16, 64, 128, 5), False),
+    (8, (2, 24, 56, 128, 5), True), (8, (2, 24, 56, 128, 6), False), (8, (1, 32, 64, 128, 5), False),
+    (8, (1, 8, 64, 128, 5), True), (8, (1, 16, 64, 128, 5), True),
     (4, (2, 28, 56, 128, 5), True), (4, (3, 24, 56, 128, 5), True), (4, (2, 28, 56, 128, 6), False),
     (16, (1, 64, 32, 128, 6), True), (16, (1, 32, 64, 256, 6), True), (16, (1, 32, 64, 256, 5), False),
 ])
