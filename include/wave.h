@@ -131,7 +131,10 @@ wave_status wave_set_receivers(wave_plan_t plan, int nrec, const double* xyz);
 
 /* Force the tiling of the forward passes (see wave_tiling); T = 1 selects the
  * plain one-step kernel.  Fields of 0 are chosen by the library.  Rejects a
- * schedule the tile-legality scheduler does not accept (WAVE_ERR_ARG). */
+ * schedule the tile-legality scheduler does not accept (WAVE_ERR_ARG).  A
+ * one-step tiling also becomes the tiling of the plan's one-step sweeps (the
+ * recompute and adjoint sweeps of wave_gradient, steps left over when nt is
+ * not a multiple of T). */
 wave_status wave_set_tiling(wave_plan_t plan, const wave_tiling* tiling);
 
 /* wave_autotune with its result cached by key: the device (name and SM
@@ -152,8 +155,10 @@ wave_status wave_get_tiling(wave_plan_t plan, wave_tiling* tiling);
  * shapes and slab lengths) with `passes` timed passes each, and keep the
  * fastest in point-steps per second (T = 1 may win: the paper's remark that
  * time tiling is only worthwhile when the loop is memory-bound).  T_only > 0
- * restricts the sweep to that T.  The plan's wavefields are scratch during
- * the sweep.  cand / ms_per_step: host arrays of up to `cap` entries (may be
+ * restricts the sweep to that T.  The fastest one-step candidate, whether
+ * or not it wins, becomes the tiling of the plan's one-step sweeps (see
+ * wave_set_tiling).  The plan's wavefields are scratch during the sweep.
+ * cand / ms_per_step: host arrays of up to `cap` entries (may be
  * NULL) receiving every timed candidate and its milliseconds per time step;
  * *ncand (may be NULL) receives how many were timed. */
 wave_status wave_autotune(wave_plan_t plan, int passes, int T_only, wave_tiling* cand, double* ms_per_step,

@@ -458,6 +458,7 @@ wave_status apply_tiling(wave_plan_t p, const wave_tiling& t)
     }
     p->tiling = t;
     p->geom = g;
+    if (g.T == 1) p->geom1 = g;  // one-step sweeps (gradient, remainders) follow a one-step tiling
     p->gen++;
     return WAVE_OK;
 }
@@ -771,8 +772,8 @@ extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave
     CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
     CK(cudaMemsetAsync(p->buf[0], 0, p->npad * 4, p->st));
     CK(cudaMemsetAsync(p->buf[1], 0, p->npad * 4, p->st));
-    double best = 1e300;
-    wave_tiling best_t = p->tiling;
+    double best = 1e300, best1 = 1e300;
+    wave_tiling best_t = p->tiling, best1_t{};
     int count = 0;
     TapSet none;
     for (auto& t : cands) {
@@ -800,12 +801,25 @@ extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave
             best = per_step;
             best_t = t;
         }
+        if (geom.T == 1 && per_step < best1) {
+            best1 = per_step;
+            best1_t = t;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ncand) *ncand = count;
     wave_status s = finish(p);
     if (s) return s;
+    // the fastest one-step tiling also runs the plan's one-step sweeps (the
+    // recompute and adjoint sweeps of the gradient, remainder steps)
+    if (best1 < 1e300) {
+        PassGeom g1;
+        if (make_geom(p->n, p->R, best1_t, &g1, nullptr)) {
+            p->geom1 = g1;
+            p->gen++;
+        }
+    }
     return apply_tiling(p, best_t);
 }
 
