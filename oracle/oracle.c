@@ -29,7 +29,7 @@
  * on the outermost space loop, which does not change any result (every
  * point is computed independently from the previous two levels).
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent (the same readings the library takes):
  *   - the damping profile d: a sponge of `sponge_width` cells on the faces in
  *     `sponge_faces`, d = dmax_a ((W - delta)/W)^2 for a point delta < W cells
  *     from a face on axis a, summed over faces and axes, with
