@@ -101,7 +101,12 @@ wave_status wave_cfl_limit(int so, const double spacing[3], double vmax, double*
 
 /* Create a plan: validates the problem, builds the FD coefficients, checks
  * the CFL limit (WAVE_ERR_CFL), allocates the wavefield buffers and converts
- * the model.  grid: host [3] = nx, ny, nz (each >= so + 1); spacing: host [3]
+ * the model.  The arguments are the paper's statement of the problem: the
+ * grid, spacing, space order, dt and squared slowness m of the acoustic
+ * example (Section "Acoustic wave equation", Fig. acoustic_devito; grid sizes
+ * as in Section "Simulation Grid Size"), plus the absorbing `damp` layer of
+ * the same figure (wave_options).  The plan owns its wavefields; the caller
+ * keeps m.  grid: host [3] = nx, ny, nz (each >= so + 1); spacing: host [3]
  * metres; so in {4, 8, 16}; dt > 0 in ms; nt >= 0 time steps;
  * m: device [nx][ny][nz] squared slowness (copied, not kept); opt may be NULL.
  * The plan is bound to the device current at the call (or opt->device). */
@@ -115,13 +120,17 @@ wave_status wave_set_model(wave_plan_t plan, const float* m);
 /* Point sources: xyz host [nsrc][3] metres, injected through trilinear
  * weights as a term of the discrete equation (L_h u -> L_h u + sum w q);
  * wavelet device [nt][nsrc] (copied).  Update n injects row n.  nsrc = 0
- * clears the sources.  The paper removes its source before tiling (Section
- * "Functional Correctness"); here it is fused into every pass. */
+ * clears the sources.  Every coordinate must be finite and inside the grid,
+ * 0 <= xyz[a] <= (n_a - 1) h_a (WAVE_ERR_ARG otherwise).  The paper removes
+ * its source before tiling (Section "Functional Correctness"); here it is
+ * fused into every pass. */
 wave_status wave_set_sources(wave_plan_t plan, int nsrc, const double* xyz, const float* wavelet);
 
 /* Receivers: xyz host [nrec][3] metres; trace n of receiver j is the
  * trilinear interpolation of u^{n+1} (the field produced by update n).
- * nrec = 0 clears them.  A dense receiver surface (at least 4096 receivers
+ * nrec = 0 clears them.  Positions follow the rule of wave_set_sources (the
+ * paper samples its receivers in the loop after the stencil, Section
+ * "Testing environment").  A dense receiver surface (at least 4096 receivers
  * whose taps all lie in one or two adjacent z quads, e.g. a grid of
  * receivers at one depth) is recorded, when the plan's passes are one-step,
  * by a gather after every pass from the new field, with the same taps,
@@ -129,8 +138,12 @@ wave_status wave_set_sources(wave_plan_t plan, int nsrc, const double* xyz, cons
  * identical). */
 wave_status wave_set_receivers(wave_plan_t plan, int nrec, const double* xyz);
 
-/* Force the tiling of the forward passes (see wave_tiling); T = 1 selects the
- * plain one-step kernel.  Fields of 0 are chosen by the library.  Rejects a
+/* Force the tiling of the forward passes (see wave_tiling).  T = 1 selects a
+ * one-step pass (one time step per pass over HBM: the plain, untiled method)
+ * in the variant that `unroll` names: 0, 1 or 2 = the block-barrier pass
+ * (wave_pass.cuh), 5 or 6 = the warp-specialised pass (wave_lean.cuh).  All
+ * one-step variants compute the same bits; the benchmark's untiled baseline is
+ * the fastest of them.  Fields of 0 are chosen by the library.  Rejects a
  * schedule the tile-legality scheduler does not accept (WAVE_ERR_ARG).  A
  * one-step tiling also becomes the tiling of the plan's one-step sweeps (the
  * recompute and adjoint sweeps of wave_gradient, steps left over when nt is
@@ -139,17 +152,24 @@ wave_status wave_set_tiling(wave_plan_t plan, const wave_tiling* tiling);
 
 /* wave_autotune with its result cached by key: the device (name and SM
  * count), the grid, the space order, T_only and the set of compiled kernel
- * variants.  A key seen before in this process applies the stored tiling
- * without timing anything; with the environment variable
+ * variants.  A key seen before in this process applies the stored tilings
+ * (the overall pick and the fastest one-step candidate, which runs the
+ * one-step sweeps) without timing anything; with the environment variable
  * WAVE_AUTOTUNE_CACHE=<path> results are also appended to that text file
- * ("key T by bz xc unroll" per line, the last line of a key wins) and looked
- * up there, so they persist across processes.  *from_cache (may be NULL) is
+ * ("key T by bz xc unroll T1 by1 bz1 xc1 unroll1" per line, the last line of
+ * a key wins) and looked up there, so they persist across processes.  *from_cache (may be NULL) is
  * set to 1 when the tiling came from the cache.  Errors as wave_autotune;
  * an unreadable or unwritable file only disables the file. */
 wave_status wave_autotune_cached(wave_plan_t plan, int passes, int T_only, int* from_cache);
 
 /* The tiling the forward passes use now (after defaults / autotuning). */
 wave_status wave_get_tiling(wave_plan_t plan, wave_tiling* tiling);
+
+/* The one-step tiling of the plan's one-step sweeps (the recompute and
+ * adjoint sweeps of wave_gradient, steps left over when nt is not a multiple
+ * of T): the built-in default, a one-step tiling given to wave_set_tiling, or
+ * the fastest one-step candidate of the last autotuning (timed or cached). */
+wave_status wave_get_sweep_tiling(wave_plan_t plan, wave_tiling* tiling);
 
 /* Time candidate tilings on the GPU for this plan (T = 1..Tmax, several tile
  * shapes and slab lengths) with `passes` timed passes each, and keep the
@@ -164,7 +184,11 @@ wave_status wave_get_tiling(wave_plan_t plan, wave_tiling* tiling);
 wave_status wave_autotune(wave_plan_t plan, int passes, int T_only, wave_tiling* cand, double* ms_per_step,
                           int cap, int* ncand);
 
-/* Forward modelling of nt steps from u^{-1}, u^0.
+/* Forward modelling of nt steps from u^{-1}, u^0: the update of Fig.
+ * acoustic_devito applied nt times (Section "Acoustic wave equation"), run
+ * T steps per pass over HBM with the plan's tiling (Chapter "Time-tiling for
+ * Devito stencils", Section "Time-Tiling"); sources and receivers are the
+ * loops that Section "Testing environment" lists around the stencil.
  * u_init: device [2][nx][ny][nz] = (u^{-1}, u^0), or NULL for zero fields.
  * rec_out: device [nt][nrec] traces, may be NULL when nrec = 0.
  * u_final: device [2][nx][ny][nz] receiving (u^{nt-1}, u^{nt}), may be NULL.
@@ -177,15 +201,25 @@ wave_status wave_forward_host(wave_plan_t plan, const float* m_host, const float
                               float* rec_host);
 
 /* Adjoint modelling: the transpose of the linear map wavelet -> traces of
- * wave_forward (zero initial fields).  rec_resid: device [nt][nrec] is
- * injected at the receivers backwards in time; src_out: device [nt][nsrc]
- * receives the adjoint field sampled at the sources.  Uses the same update
- * (L_h symmetric, damping diagonal), with receivers and sources swapping
- * roles; see the gradient below. */
-wave_status wave_adjoint(wave_plan_t plan, const float* rec_resid, float* src_out);
+ * wave_forward (zero initial fields).  The paper has no adjoint; the map is
+ * the discrete update of Fig. acoustic_devito, whose L_h is symmetric and
+ * whose damping is diagonal, so its transpose is the same update run on the
+ * time-reversed residual with the source and receiver loops of Section
+ * "Testing environment" swapping roles (same kernels, same tiling).
+ * rec_resid: device [nt][nrec] is injected at the receivers backwards in
+ * time.  src_out: device [nt][nsrc] receives the adjoint field sampled at the
+ * sources, or NULL.  v_final: device [2][nx][ny][nz] receives the last two
+ * levels of the adjoint field in the layout of wave_forward's u_final (the
+ * level before the last, then the last, which is the adjoint field at forward
+ * time 0), or NULL.  Both may be NULL.  Synchronises the plan's stream. */
+wave_status wave_adjoint(wave_plan_t plan, const float* rec_resid, float* src_out, float* v_final);
 
 /* Misfit J = 1/2 sum (rec - d_obs)^2 of the plan's sources and receivers and
- * its gradient with respect to m (adjoint state):
+ * its gradient with respect to m (adjoint state).  The paper computes no
+ * gradient; this is the exact gradient of the discrete update of Fig.
+ * acoustic_devito, and its checkpoints trade memory for recomputation as the
+ * buffered time dimension of Section "Time Dimension Buffering" trades it
+ * for a bounded time tile:
  *   dJ/dm = - sum_n mu^{n+1} (u^{n+1} - 2u^n + u^{n-1}) / dt^2,
  * mu the adjoint field driven by rec - d_obs.  d_obs: device [nt][nrec];
  * grad_m: device [nx][ny][nz]; misfit: host double (may be NULL).
@@ -219,9 +253,14 @@ wave_status wave_profile_read(wave_plan_t plan, int reset, long long* pass_launc
  * summation order as the traces of wave_forward, so sampling the field
  * wave_forward returns reproduces its last trace row.
  * grid, spacing: host [3] (cells, metres); u: device [nx][ny][nz] float32;
- * xyz: host [nrec][3] metres; rec: device [nrec] float32, written on `stream`
- * (a cudaStream_t, NULL = legacy default stream); nothing is synchronised.
- * At most 65536 receivers per call (WAVE_ERR_ARG beyond that).
+ * xyz: host [nrec][3] metres, each coordinate finite and inside
+ * [0, (n_a - 1) h_a] (WAVE_ERR_ARG otherwise, as in wave_set_receivers);
+ * rec: device [nrec] float32, written on `stream` (a cudaStream_t, NULL =
+ * legacy default stream); nothing is synchronised.  The positions are
+ * copied to the device on `stream`: from pageable memory the copy is done
+ * before the call returns, but from pinned memory it runs later, so a pinned
+ * xyz must stay valid and unchanged until the work queued on `stream` has
+ * run.  At most 65536 receivers per call (WAVE_ERR_ARG beyond that).
  *
  * The tap slots live in one static device array (5.75 MiB, held by every GPU
  * that loads the library until the process exits).  Every call shares it and

@@ -80,11 +80,12 @@ def load(build_if_missing: bool = True):
             "wave_set_receivers": (st, [_VP, ctypes.c_int, _DP]),
             "wave_set_tiling": (st, [_VP, ctypes.POINTER(Tiling)]),
             "wave_get_tiling": (st, [_VP, ctypes.POINTER(Tiling)]),
+            "wave_get_sweep_tiling": (st, [_VP, ctypes.POINTER(Tiling)]),
             "wave_autotune": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tiling), _DP, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int)]),
             "wave_forward": (st, [_VP, _VP, _VP, _VP]),
             "wave_forward_host": (st, [_VP, _VP, _VP, _VP]),
-            "wave_adjoint": (st, [_VP, _VP, _VP]),
+            "wave_adjoint": (st, [_VP, _VP, _VP, _VP]),
             "wave_gradient": (st, [_VP, _VP, _VP, _DP, ctypes.c_int]),
             "wave_plan_destroy": (st, [_VP]),
             "wave_last_error": (ctypes.c_char_p, []),
@@ -255,6 +256,13 @@ class WavePlan:
         _check(self._lib.wave_get_tiling(self._h, ctypes.byref(t)))
         return t.as_tuple()
 
+    def get_sweep_tiling(self):
+        """The one-step tiling of the plan's one-step sweeps (gradient recompute
+        and adjoint sweeps, remainder steps)."""
+        t = Tiling()
+        _check(self._lib.wave_get_sweep_tiling(self._h, ctypes.byref(t)))
+        return t.as_tuple()
+
     def autotune(self, passes=3, T_only=0, cap=256):
         cands = (Tiling * cap)()
         ms = (ctypes.c_double * cap)()
@@ -292,12 +300,18 @@ class WavePlan:
         _check(self._lib.wave_forward_host(self._h, hp(m_host), hp(wavelet_host), hp(rec_host)))
         return rec_host
 
-    def adjoint(self, rec_resid, src_out=None):
+    def adjoint(self, rec_resid, src_out=None, want_final=False, v_final=None):
+        """Adjoint traces at the sources [nt, nsrc]; with want_final (or a
+        given v_final) also the last two adjoint levels [2, nx, ny, nz]:
+        returns src_out, or (src_out, v_final) when a final field is asked."""
         torch = _torch()
         if src_out is None:
             src_out = torch.empty((self.nt, self.nsrc), dtype=torch.float32, device=self.device)
-        _check(self._lib.wave_adjoint(self._h, _dev_ptr(rec_resid, "rec_resid"), _dev_ptr(src_out, "src_out")))
-        return src_out
+        if want_final and v_final is None:
+            v_final = torch.empty((2,) + self.shape, dtype=torch.float32, device=self.device)
+        _check(self._lib.wave_adjoint(self._h, _dev_ptr(rec_resid, "rec_resid"), _dev_ptr(src_out, "src_out"),
+                                      _dev_ptr(v_final, "v_final") if v_final is not None else None))
+        return (src_out, v_final) if v_final is not None else src_out
 
     def gradient(self, d_obs, checkpoint_every=0, grad_out=None):
         """(misfit J, dJ/dm [nx, ny, nz]) for observed traces d_obs [nt, nrec]."""

@@ -12,10 +12,27 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <string>
 
 #include "wave_host.h"
 
 namespace wave {
+
+bool positions_valid(int count, const double* xyz, const double h[3], const int n[3], std::string* why)
+{
+    for (int p = 0; p < count; ++p)
+        for (int a = 0; a < 3; ++a) {
+            const double c = xyz[3 * p + a];
+            if (!std::isfinite(c) || c < 0.0 || c > (n[a] - 1) * h[a]) {
+                if (why)
+                    *why = "position " + std::to_string(p) + " axis " + std::to_string(a) + " = " +
+                           std::to_string(c) + " m is not finite or lies outside [0, (n-1) h] = [0, " +
+                           std::to_string((n[a] - 1) * h[a]) + "]";
+                return false;
+            }
+        }
+    return true;
+}
 
 int trilinear_taps(const double xyz[3], const double h[3], const int n[3], Tap out[8])
 {

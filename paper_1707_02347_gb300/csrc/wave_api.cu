@@ -139,6 +139,7 @@ struct wave_plan_s {
     float c0 = 0.f, cx[kMaxR] = {}, cy[kMaxR] = {}, cz[kMaxR] = {};
     // tiling
     wave_tiling tiling{};
+    wave_tiling tiling1{};  // tiling of the one-step sweeps (geom1)
     PassGeom geom, geom1;
     // tensor maps: (pointer, box rows, box cols) -> map
     std::map<std::tuple<const void*, int, int>, CUtensorMap> maps;
@@ -458,7 +459,11 @@ wave_status apply_tiling(wave_plan_t p, const wave_tiling& t)
     }
     p->tiling = t;
     p->geom = g;
-    if (g.T == 1) p->geom1 = g;  // one-step sweeps (gradient, remainders) follow a one-step tiling
+    if (g.T == 1) {
+        // one-step sweeps (gradient, remainders) follow a one-step tiling
+        p->geom1 = g;
+        p->tiling1 = t;
+    }
     p->gen++;
     return WAVE_OK;
 }
@@ -689,7 +694,8 @@ extern "C" wave_status wave_plan_create(wave_plan_t* out, const int grid[3], con
     if (s) return bail(s);
     // the one-step geometry (remainder steps, adjoint, gradient)
     std::string why;
-    if (!make_geom(p->n, p->R, default_tiling(p->n, p->R, 1), &p->geom1, &why))
+    p->tiling1 = default_tiling(p->n, p->R, 1);
+    if (!make_geom(p->n, p->R, p->tiling1, &p->geom1, &why))
         return bail(fail(WAVE_ERR_ARG, "no one-step tiling: " + why));
     wave_tiling t = o.tiling;
     if (t.T <= 0 && t.by <= 0 && t.bz <= 0 && t.xc <= 0) {
@@ -721,6 +727,8 @@ extern "C" wave_status wave_set_sources(wave_plan_t p, int nsrc, const double* x
     if (!p || nsrc < 0) return fail(WAVE_ERR_ARG, "wave_set_sources: bad argument");
     if (nsrc > 0 && (!xyz || (!wavelet && p->nt > 0)))
         return fail(WAVE_ERR_ARG, "wave_set_sources: null positions or wavelet");
+    std::string why;
+    if (!positions_valid(nsrc, xyz, p->h, p->n, &why)) return fail(WAVE_ERR_ARG, "wave_set_sources: " + why);
     DeviceGuard g(p->dev);
     p->src_xyz.assign(xyz, xyz + 3 * static_cast<size_t>(nsrc));
     p->adj_ready = false;
@@ -740,6 +748,8 @@ extern "C" wave_status wave_set_receivers(wave_plan_t p, int nrec, const double*
 {
     if (!p || nrec < 0) return fail(WAVE_ERR_ARG, "wave_set_receivers: bad argument");
     if (nrec > 0 && !xyz) return fail(WAVE_ERR_ARG, "wave_set_receivers: null positions");
+    std::string why;
+    if (!positions_valid(nrec, xyz, p->h, p->n, &why)) return fail(WAVE_ERR_ARG, "wave_set_receivers: " + why);
     DeviceGuard g(p->dev);
     p->rec_xyz.assign(xyz, xyz + 3 * static_cast<size_t>(nrec));
     p->adj_ready = false;
@@ -757,6 +767,13 @@ extern "C" wave_status wave_get_tiling(wave_plan_t p, wave_tiling* t)
 {
     if (!p || !t) return fail(WAVE_ERR_ARG, "wave_get_tiling: null argument");
     *t = p->tiling;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_get_sweep_tiling(wave_plan_t p, wave_tiling* t)
+{
+    if (!p || !t) return fail(WAVE_ERR_ARG, "wave_get_sweep_tiling: null argument");
+    *t = p->tiling1;
     return WAVE_OK;
 }
 
@@ -817,6 +834,7 @@ extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave
         PassGeom g1;
         if (make_geom(p->n, p->R, best1_t, &g1, nullptr)) {
             p->geom1 = g1;
+            p->tiling1 = best1_t;
             p->gen++;
         }
     }
@@ -828,10 +846,14 @@ namespace {
 // Autotuning results by key: device, grid, space order, T restriction and the
 // set of compiled kernel variants (a different build never reuses an entry).
 // Kept for the process; with WAVE_AUTOTUNE_CACHE=<path> also appended to, and
-// looked up in, that text file (one "key T by bz xc variant" line per result,
-// the last line of a key wins).
+// looked up in, that text file (one line per result: the key, the overall
+// pick "T by bz xc variant", then the fastest one-step tiling in the same
+// five fields; the last line of a key wins).
+struct TuneEntry {
+    wave_tiling best, best1;
+};
 std::mutex g_tune_mu;
-std::map<std::string, wave_tiling> g_tune;
+std::map<std::string, TuneEntry> g_tune;
 
 std::string tune_key(wave_plan_t p, int T_only)
 {
@@ -853,7 +875,7 @@ std::string tune_key(wave_plan_t p, int T_only)
     return buf;
 }
 
-bool tune_lookup(const std::string& key, wave_tiling* t)
+bool tune_lookup(const std::string& key, TuneEntry* t)
 {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);
@@ -869,8 +891,10 @@ bool tune_lookup(const std::string& key, wave_tiling* t)
     char line[512];
     while (std::fgets(line, sizeof(line), f)) {
         char k[300];
-        wave_tiling r{};
-        if (std::sscanf(line, "%299s %d %d %d %d %d", k, &r.T, &r.by, &r.bz, &r.xc, &r.unroll) == 6 && key == k) {
+        TuneEntry r{};
+        if (std::sscanf(line, "%299s %d %d %d %d %d %d %d %d %d %d", k, &r.best.T, &r.best.by, &r.best.bz, &r.best.xc,
+                        &r.best.unroll, &r.best1.T, &r.best1.by, &r.best1.bz, &r.best1.xc, &r.best1.unroll) == 11 &&
+            key == k) {
             *t = r;
             found = true;
         }
@@ -880,14 +904,15 @@ bool tune_lookup(const std::string& key, wave_tiling* t)
     return found;
 }
 
-void tune_store(const std::string& key, const wave_tiling& t)
+void tune_store(const std::string& key, const TuneEntry& t)
 {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[key] = t;
     const char* path = std::getenv("WAVE_AUTOTUNE_CACHE");
     if (!path || !*path) return;
     if (FILE* f = std::fopen(path, "a")) {
-        std::fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), t.T, t.by, t.bz, t.xc, t.unroll);
+        std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d\n", key.c_str(), t.best.T, t.best.by, t.best.bz, t.best.xc,
+                     t.best.unroll, t.best1.T, t.best1.by, t.best1.bz, t.best1.xc, t.best1.unroll);
         std::fclose(f);
     }
 }
@@ -900,17 +925,22 @@ extern "C" wave_status wave_autotune_cached(wave_plan_t p, int passes, int T_onl
     if (from_cache) *from_cache = 0;
     DeviceGuard g(p->dev);
     const std::string key = tune_key(p, T_only);
-    wave_tiling t{};
-    PassGeom geom;
-    if (tune_lookup(key, &t) && make_geom(p->n, p->R, t, &geom, nullptr)) {
-        wave_status s = apply_tiling(p, t);
+    TuneEntry t{};
+    PassGeom geom, geom1;
+    if (tune_lookup(key, &t) && make_geom(p->n, p->R, t.best, &geom, nullptr) &&
+        t.best1.T == 1 && make_geom(p->n, p->R, t.best1, &geom1, nullptr)) {
+        wave_status s = apply_tiling(p, t.best);
         if (s) return s;
+        // the stored fastest one-step tiling runs the one-step sweeps, as after timing
+        p->geom1 = geom1;
+        p->tiling1 = t.best1;
+        p->gen++;
         if (from_cache) *from_cache = 1;
         return WAVE_OK;
     }
     wave_status s = wave_autotune(p, passes, T_only, nullptr, nullptr, 0, nullptr);
     if (s) return s;
-    tune_store(key, p->tiling);
+    tune_store(key, TuneEntry{p->tiling, p->tiling1});
     return WAVE_OK;
 }
 
@@ -953,9 +983,9 @@ extern "C" wave_status wave_forward_host(wave_plan_t p, const float* m_host, con
     return finish(p);
 }
 
-extern "C" wave_status wave_adjoint(wave_plan_t p, const float* rec_resid, float* src_out)
+extern "C" wave_status wave_adjoint(wave_plan_t p, const float* rec_resid, float* src_out, float* v_final)
 {
-    if (!p || !rec_resid || !src_out) return fail(WAVE_ERR_ARG, "wave_adjoint: null argument");
+    if (!p || !rec_resid) return fail(WAVE_ERR_ARG, "wave_adjoint: null argument");
     DeviceGuard g(p->dev);
     wave_status s = ensure_adjoint_taps(p);
     if (s) return s;
@@ -979,11 +1009,14 @@ extern "C" wave_status wave_adjoint(wave_plan_t p, const float* rec_resid, float
     }
     s = advance(p, &f, p->adj, wrev, slots, 0, p->nt, true);
     if (s) return s;
-    if (p->adj.ntaps > 0)
-        CKL(launch_rec_reduce(slots, p->adj.rec_tptr, p->adj.rec_tw, orev, p->nt, nsrc, p->adj.ntaps, p->st));
-    else
-        CK(cudaMemsetAsync(orev, 0, obytes, p->st));
-    CKL(launch_reverse_rows(orev, src_out, p->nt, nsrc, p->st));
+    if (src_out) {
+        if (p->adj.ntaps > 0)
+            CKL(launch_rec_reduce(slots, p->adj.rec_tptr, p->adj.rec_tw, orev, p->nt, nsrc, p->adj.ntaps, p->st));
+        else
+            CK(cudaMemsetAsync(orev, 0, obytes, p->st));
+        CKL(launch_reverse_rows(orev, src_out, p->nt, nsrc, p->st));
+    }
+    if (v_final) CKL(launch_final_state(f.u, f.v, v_final, p->n[0], p->n[1], p->n[2], p->nzp, p->st));
     return finish(p);
 }
 

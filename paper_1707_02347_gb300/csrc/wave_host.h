@@ -48,6 +48,10 @@ struct Tap {
     int i, j, k;
     double w;
 };
+// True if every coordinate of the count points is finite and inside
+// [0, (n_a - 1) h_a] (the grid's extent), else false with the first offender
+// in *why.  Checked before any position reaches trilinear_taps.
+bool positions_valid(int count, const double* xyz, const double h[3], const int n[3], std::string* why);
 // Corners of the cell containing xyz with non-zero weight and inside the grid,
 // in corner order c = 4 dx + 2 dy + dz.
 int trilinear_taps(const double xyz[3], const double h[3], const int n[3], Tap out[8]);

@@ -127,9 +127,13 @@ extern "C" wave_status wave_sample_noalloc(const int grid[3], const double spaci
         return wave::fail(WAVE_ERR_ARG, "wave_sample_noalloc: nrec must be in [0, " + std::to_string(kMaxReceivers) +
                                             "] (the static slot array holds that many receivers)");
     for (int a = 0; a < 3; ++a)
-        if (grid[a] < 1 || !(spacing[a] > 0.0))
+        if (grid[a] < 1 || !(spacing[a] > 0.0) || !std::isfinite(spacing[a]))
             return wave::fail(WAVE_ERR_ARG, "wave_sample_noalloc: grid extents and spacing must be positive");
     if (nrec == 0) return WAVE_OK;
+    // the kernel turns xyz / h into cell indices: only finite positions inside the grid get there
+    std::string why;
+    if (!wave::positions_valid(nrec, xyz, spacing, grid, &why))
+        return wave::fail(WAVE_ERR_ARG, "wave_sample_noalloc: " + why);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return wave::fail(WAVE_ERR_CUDA, "wave_sample_noalloc: no current device");
