@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-untiled", action="store_true")
+    ap.add_argument("--no-gradient", action="store_true", help="leave out the FWI gradient record")
     ap.add_argument("--tiling", default="", help="force T,by,bz,xc[,unroll] instead of autotuning")
     ap.add_argument("--so", type=int, default=8, help="space order of the tiled512 workload (4, 8 or 16)")
     ap.add_argument("--workload", choices=["tiled512", "so16", "batched", "gradient"], default="tiled512",
@@ -77,7 +78,7 @@ class ClockSampler:
         self.proc = None
         self.thread = None
         self.gpu_id = gpu_id
-        self.active = False
+        self.active = False  # False, or the name of the timed region being sampled
 
     def start(self):
         try:
@@ -107,8 +108,10 @@ class ClockSampler:
         if self.thread is not None:
             self.thread.join(timeout=5)
 
-    def summary(self):
-        load = [p for a, p in self.samples if a]
+    def summary(self, region=None):
+        """Clocks of the samples taken while a region was active (any region,
+        or only `region`)."""
+        load = [p for a, p in self.samples if a and (region is None or a == region)]
         if not load:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
 
@@ -242,7 +245,7 @@ def cpu_baseline(w):
     return out
 
 
-def run_batched(args, W, inputs, dev, world, rank, dist):
+def run_batched(args, W, inputs, dev, world, rank, dist, local):
     """24 shots, grids drawn seeded from [128,320] x [128,320] x [128,256],
     SO alternating 4 / 8, Ricker 8-15 Hz, each with its own autotuned tiling:
     observed data by one batched forward on the true models, then the FWI
@@ -275,6 +278,9 @@ def run_batched(args, W, inputs, dev, world, rank, dist):
         m_true.append(m)
         pts += float(np.prod(shape)) * nt
     batch = W.WaveBatch(plans)
+    clk = ClockSampler(gpu_uuid_of(dev, local))
+    clk.start()
+    time.sleep(0.5)
     # batched forward on the true models: the observed data, and its timing
     recs = batch.forward()
     for _ in range(args.warmup):
@@ -282,11 +288,14 @@ def run_batched(args, W, inputs, dev, world, rank, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    clk.active = "forward"
     t0 = time.perf_counter()
     for _ in range(args.steps):
         batch.forward(recs)
     torch.cuda.synchronize()
-    el_f = replicas.max_over_ranks(time.perf_counter() - t0, dev)
+    el_f = time.perf_counter() - t0
+    clk.active = False
+    el_f = replicas.max_over_ranks(el_f, dev)
     d_obs = [r.clone() for r in recs]
     for p, m in zip(plans, m_true):
         p.set_model(m * (1.03 ** 2))
@@ -296,11 +305,15 @@ def run_batched(args, W, inputs, dev, world, rank, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    clk.active = "gradient"
     t0 = time.perf_counter()
     for _ in range(args.steps):
         mis, _ = batch.gradient(d_obs, checkpoint_every=40, grads=grads)
     torch.cuda.synchronize()
-    el_g = replicas.max_over_ranks(time.perf_counter() - t0, dev)
+    el_g = time.perf_counter() - t0
+    clk.active = False
+    clk.stop()
+    el_g = replicas.max_over_ranks(el_g, dev)
     ok = all(np.isfinite(mis)) and all(bool(torch.isfinite(g).all()) for g in grads)
     if rank == 0:
         out = {"metric": "FWI gradient s/shot", "value": el_g / args.steps / (len(plans) * world),
@@ -313,25 +326,39 @@ def run_batched(args, W, inputs, dev, world, rank, dist):
                           "shots_per_rank": len(plans), "gradients_finite": ok,
                           "tilings": [p.get_tiling() for p in plans]},
                "forward": {"value": pts * world * args.steps / el_f / 1e9, "unit": "GPt/s",
-                           "ms_per_step": 1e3 * el_f / args.steps},
-               "gradient_point_steps_per_s": pts * world * args.steps / el_g}
+                           "ms_per_step": 1e3 * el_f / args.steps, "clocks": clk.summary("forward")},
+               "gradient_point_steps_per_s": pts * world * args.steps / el_g,
+               "clocks": clk.summary("gradient")}
         print(json.dumps(out), flush=True)
     batch.close()
     for p in plans:
         p.close()
 
 
-def run_gradient(args, W, inputs, dev, world, rank, dist):
+def gpu_uuid_of(dev, local):
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+
+
+def gradient_record(args, W, inputs, dev, world, dist, clk, steps=None, warmup=None):
     """FWI gradient of one shot: 256^3, SO8, 800 steps, 10 Hz Ricker, 256
     receivers on a line at 20 m; data from the seeded true model (seed 3),
     gradient on the true model blurred with sigma = 10 cells, checkpoints
     every 40 steps.  Seconds per shot (forward + checkpoints + recompute +
-    adjoint + imaging condition)."""
+    adjoint + imaging condition), timed with the clocks sampled under the
+    region name "gradient"."""
     import numpy as np
     import torch
 
     from paper_1707_02347_gb300 import replicas
 
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     n, nt = 256, min(args.nt, 800)
     w = inputs.layered_forward((n, n, n), 8, nt, seed=3, f=10.0, h=10.0, sponge_width=10, nrec_line=256)
     v_true = 1.0 / np.sqrt(w.m.astype(np.float64))
@@ -345,27 +372,48 @@ def run_gradient(args, W, inputs, dev, world, rank, dist):
     d_obs, _ = plan.forward()
     d_obs = d_obs.clone()
     plan.set_model(m0)
-    for _ in range(max(args.warmup, 1)):
-        J, g = plan.gradient(d_obs, checkpoint_every=40)
+    grad = torch.empty(w.shape, dtype=torch.float32, device=dev)
+    for _ in range(max(warmup, 1)):
+        J, g = plan.gradient(d_obs, checkpoint_every=40, grad_out=grad)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    clk.active = "gradient"
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        J, g = plan.gradient(d_obs, checkpoint_every=40)
+    for _ in range(steps):
+        J, g = plan.gradient(d_obs, checkpoint_every=40, grad_out=grad)
     torch.cuda.synchronize()
-    el = replicas.max_over_ranks(time.perf_counter() - t0, dev)
-    if rank == 0:
-        out = {"metric": "FWI gradient s/shot", "value": el / args.steps, "unit": "s/shot", "n_gpus": world,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-               "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic",
-               "config": {"workload": "FWI gradient 256x256x256, h=10 m, SO8, %d steps, 10 Hz Ricker, 256 receivers "
-                                      "at 20 m, true model seed 3, start = true blurred sigma 10, checkpoint "
-                                      "every 40 steps" % nt, "tiling": list(plan.get_tiling()), "misfit": J,
-                          "point_steps_per_s": float(n) ** 3 * nt / (el / args.steps)}}
-        print(json.dumps(out), flush=True)
+    el = time.perf_counter() - t0
+    clk.active = False
+    el = replicas.max_over_ranks(el, dev)
+    rec = {"metric": "FWI gradient s/shot", "value": el / steps, "unit": "s/shot", "higher_is_better": False,
+           "steps": steps, "warmup": warmup,
+           "workload": "FWI gradient 256x256x256, h=10 m, SO8, %d steps, 10 Hz Ricker, 256 receivers at 20 m, "
+                       "true model seed 3, start = true blurred sigma 10, checkpoint every 40 steps" % nt,
+           "tiling": list(plan.get_tiling()), "sweep_tiling": list(plan.get_sweep_tiling()), "misfit": J,
+           "gradient_finite": bool(torch.isfinite(g).all()),
+           "point_steps_per_s": float(n) ** 3 * nt / (el / steps), "clocks": clk.summary("gradient")}
     plan.close()
+    return rec
+
+
+def run_gradient(args, W, inputs, dev, world, rank, dist, local):
+    """The FWI gradient workload on its own line (see gradient_record)."""
+    clk = ClockSampler(gpu_uuid_of(dev, local))
+    clk.start()
+    time.sleep(0.5)
+    try:
+        g = gradient_record(args, W, inputs, dev, world, dist, clk)
+    finally:
+        clk.stop()
+    if rank == 0:
+        out = {"metric": g["metric"], "value": g["value"], "unit": "s/shot", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * g["value"], "higher_is_better": False,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": g["workload"], "tiling": g["tiling"], "sweep_tiling": g["sweep_tiling"],
+                          "misfit": g["misfit"], "point_steps_per_s": g["point_steps_per_s"]},
+               "clocks": g["clocks"]}
+        print(json.dumps(out), flush=True)
 
 
 def main():
@@ -398,10 +446,10 @@ def main():
         torch.cuda.synchronize()
 
     if args.workload == "batched":
-        run_batched(args, W, inputs, dev, world, rank, dist)
+        run_batched(args, W, inputs, dev, world, rank, dist, local)
         return
     if args.workload == "gradient":
-        run_gradient(args, W, inputs, dev, world, rank, dist)
+        run_gradient(args, W, inputs, dev, world, rank, dist, local)
         return
     n = args.grid or 512
     if args.workload == "so16":
@@ -425,30 +473,32 @@ def main():
                           sponge_faces=w.sponge_faces, vmax=w.vmax, stream=stream)
     plan.set_sources(w.src_xyz, wav)
     plan.set_receivers(w.rec_xyz)
-    # autotune: the best T = 1 (plain one-step) tiling and the best overall
+    # autotune: the fastest tiling overall (the headline), the fastest one-step
+    # (T = 1, untiled) tiling and the fastest time-tiled (T >= 2) tiling
     if args.tiling:
         best = tuple(int(x) for x in args.tiling.split(","))
         plan.set_tiling(best)
+        best = plan.get_tiling()
         tuned = []
     else:
         tuned = plan.autotune(passes=3)
         best = plan.get_tiling()
-    if not args.no_untiled:
-        one = [t for t in tuned if t[0][0] == 1]
-        untiled_tiling = min(one, key=lambda c: c[1])[0] if one else (1, 16, 64, 128)
-        multi = [t for t in tuned if t[0][0] >= 2]
-        tiled_tiling = min(multi, key=lambda c: c[1])[0] if multi else None
+    one = [t for t in tuned if t[0][0] == 1]
+    multi = [t for t in tuned if t[0][0] >= 2]
+    untiled_tiling = min(one, key=lambda c: c[1])[0] if one else None
+    tiled_tiling = min(multi, key=lambda c: c[1])[0] if multi else None
 
     rec = torch.empty((w.nt, w.rec_xyz.shape[0]), dtype=torch.float32, device=dev)
     lib = W.load()
-    import ctypes
 
-    def timed(tiling, K, Wm, profile):
+    def timed(tiling, K, Wm):
+        """K forward runs in `tiling` after Wm untimed ones: (ms, pass launches,
+        summed pass-kernel ms, point-steps of those passes, kernels launched)."""
         plan.set_tiling(tiling)
         for _ in range(Wm):
             plan.forward(rec_out=rec)
         lib.wave_profile_read(plan._h, 1, None, None, None, None)
-        lib.wave_profile_enable(plan._h, 1 if profile else 0)
+        lib.wave_profile_enable(plan._h, 1)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -468,58 +518,64 @@ def main():
         lib.wave_profile_enable(plan._h, 0)
         return ms, nl.value, pms.value, pst.value, lau.value
 
-    gpu_uuid = None
-    try:
-        u = str(torch.cuda.get_device_properties(dev).uuid)
-        gpu_uuid = u if u.startswith("GPU-") else "GPU-" + u
-    except Exception:
-        gpu_uuid = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
-    clk = ClockSampler(gpu_uuid)
+    hbm, smmax, peak_kind = peaks()
+    clk = ClockSampler(gpu_uuid_of(dev, local))
     clk.start()
     time.sleep(0.5)
-    clk.active = True
-    ms, nl, pass_ms, pass_pts, launches = timed(best, args.steps, args.warmup, True)
-    clk.active = False
-    value = world * args.steps * npts * w.nt / (ms * 1e-3) / 1e9
-    ms_step = ms / args.steps
+    runs = {}
 
-    untiled = None
-    if not args.no_untiled:
-        ms1, nl1, pms1, pst1, la1 = timed(untiled_tiling, args.steps, args.warmup, True)
-        v1 = world * args.steps * npts * w.nt / (ms1 * 1e-3) / 1e9
-        untiled = {"value": v1, "unit": "GPt/s", "ms_per_step": ms1 / args.steps, "tiling": list(untiled_tiling),
-                   "bytes_per_point_step": 20, "kernel_avg_launch_ms": pms1 / max(nl1, 1),
-                   "speedup_tiled_over_untiled": value / v1}
-        if tiled_tiling is not None and tiled_tiling[0] >= 2:
-            # the best time-tiled pass (T >= 2) on the same run, whether or not it wins
-            ms2, nl2, pms2, pst2, la2 = timed(tiled_tiling, args.steps, args.warmup, True)
-            v2 = world * args.steps * npts * w.nt / (ms2 * 1e-3) / 1e9
-            T2 = tiled_tiling[0]
-            hbm_pk = peaks()[0]
-            launch_s = pms2 / max(nl2, 1) * 1e-3
-            wf2, _ = kernel_traffic(T2, so, tiled_tiling[4] if len(tiled_tiling) > 4 else 0,
-                                    "smem_wavefronts_per_point")
-            untiled["best_time_tiled"] = {
-                "value": v2, "unit": "GPt/s", "ms_per_step": ms2 / args.steps, "tiling": list(tiled_tiling),
-                "speedup_over_untiled": v2 / v1, "algorithmic_bytes_per_point_step": 20.0 / T2,
+    def measure(tiling):
+        key = tuple(tiling)
+        if key not in runs:
+            clk.active = "forward"
+            ms, nl, pms, pst, la = timed(tiling, args.steps, args.warmup)
+            clk.active = False
+            runs[key] = dict(ms=ms, launches=nl, pass_ms=pms, pass_pts=pst, kernels=la)
+        return runs[key]
+
+    def forward_record(tiling, r):
+        """GPt/s of a forward run in `tiling`, with its pass kernel against the
+        compulsory-traffic roofline: 16 B per grid point per pass (read
+        u^{n-1}, u^n and m, write u^{n+T}; 16/T B per point-step), and the
+        20 B the design moves (u, v, kappa in; u, v out) beside it."""
+        T = tiling[0]
+        launch_s = r["pass_ms"] / max(r["launches"], 1) * 1e-3
+        v = world * args.steps * npts * w.nt / (r["ms"] * 1e-3) / 1e9
+        return {"value": v, "unit": "GPt/s", "ms_per_step": r["ms"] / args.steps, "tiling": list(tiling),
+                "kernel": kernel_name(so, T, tiling[4] if len(tiling) > 4 else 0),
                 "pass_avg_launch_ms": launch_s * 1e3,
-                "hbm_frac": 20.0 * npts / launch_s / 1e9 / hbm_pk,
-                "smem_frac": (wf2 * npts * 128 / launch_s / 1e9 / (152 * 128 * peaks()[1] * 1e6 / 1e9)
-                              if wf2 is not None else None)}
-    clk.stop()
+                "compulsory_bytes_per_point_step": 16.0 / T,
+                "hbm_frac": 16.0 * npts / launch_s / 1e9 / hbm,
+                "design_bytes_per_point_step": 20.0 / T,
+                "hbm_frac_design_bytes": 20.0 * npts / launch_s / 1e9 / hbm}
 
-    hbm, smmax, peak_kind = peaks()
+    rb = measure(best)
+    value = world * args.steps * npts * w.nt / (rb["ms"] * 1e-3) / 1e9
+    ms_step = rb["ms"] / args.steps
+    untiled = tiled = None
+    if not args.no_untiled:
+        if untiled_tiling is not None:
+            untiled = forward_record(untiled_tiling, measure(untiled_tiling))
+        if tiled_tiling is not None:
+            tiled = forward_record(tiled_tiling, measure(tiled_tiling))
+            if untiled is not None:
+                tiled["speedup_over_untiled"] = tiled["value"] / untiled["value"]
+
     T = best[0]
-    bytes_per_launch = 20.0 * npts  # read u, v, kappa; write u, v (once per pass)
-    avg_launch_s = (pass_ms / max(nl, 1)) * 1e-3
-    achieved = bytes_per_launch / avg_launch_s / 1e9
     variant = best[4] if len(best) > 4 else 0
+    avg_launch_s = (rb["pass_ms"] / max(rb["launches"], 1)) * 1e-3
+    bytes_per_launch = 16.0 * npts  # compulsory: read u^{n-1}, u^n, m; write u^{n+T}
+    achieved = bytes_per_launch / avg_launch_s / 1e9
     traffic_pp, src_hash = kernel_traffic(T, so, variant)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic_pp * npts if traffic_pp is not None else None,
             "kernel": kernel_name(so, T, variant), "peak_kind": peak_kind,
-            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-            "launches_timed": nl, "kernel_source_sha256_16": src_hash}
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "algorithmic_bytes_note": "compulsory 16 B per grid point and pass (u^{n-1}, u^n, m in; u^{n+T} out)",
+            "design_bytes_per_launch": 20.0 * npts,
+            "frac_design_bytes": 20.0 * npts / avg_launch_s / 1e9 / hbm,
+            "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": rb["launches"],
+            "kernel_source_sha256_16": src_hash}
     flops_pp = 9 * (so // 2) + 5  # per point-step: 3 axes x r pairs x (add + fma), centre, update
     fp32_peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
     # shared memory: one 128-byte wavefront per SM and clock
@@ -532,6 +588,7 @@ def main():
                      "frac": smem_ach / smem_peak, "wavefronts_per_point": wf_pp,
                      "note": "shared-memory load/store wavefronts of one launch (ncu, 128 B each) over the "
                              "measured launch time, vs one wavefront per SM per clock at max clock"}
+    pass_ms, pass_pts = rb["pass_ms"], rb["pass_pts"]
     roof_alu = {"bound": "alu", "achieved": flops_pp * pass_pts / (pass_ms * 1e-3) / 1e12, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": flops_pp * pass_pts / (pass_ms * 1e-3) / 1e12 / fp32_peak,
                 "flops_per_point_step": flops_pp,
@@ -546,11 +603,13 @@ def main():
         for _ in range(max(1, args.warmup)):
             plan.forward_host(m_h, w_h, r_h)
         barrier()
+        clk.active = "e2e"
         t0 = time.perf_counter()
         for _ in range(args.steps):
             plan.forward_host(m_h, w_h, r_h)
         barrier()
         el = time.perf_counter() - t0
+        clk.active = False
         if dist is not None:
             t = torch.tensor([el], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -558,8 +617,17 @@ def main():
         e2e = {"value": world * args.steps * npts * w.nt / el / 1e9, "unit": "GPt/s",
                "h2d_bytes_per_step": int(m_h.numel() * 4 + w_h.numel() * 4),
                "d2h_bytes_per_step": int(r_h.numel() * 4)}
+        plan.set_tiling(best)
+        plan.forward(rec_out=rec)
         ref_rec = rec.cpu()
         assert torch.equal(ref_rec, r_h), "host-buffer path differs from the device path"
+    plan.close()
+
+    # the metric's third quantity: FWI gradient seconds per shot (256^3, SO8, 800 steps)
+    grad = None
+    if args.workload == "tiled512" and not args.no_gradient:
+        grad = gradient_record(args, W, inputs, dev, world, dist, clk)
+    clk.stop()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -572,12 +640,15 @@ def main():
                "config": {"workload": workload_name, "grid": list(w.shape), "so": so, "nt": w.nt, "tiling": list(best),
                           "dt_ms": w.dt, "l2": "inputs larger than L2 (each field %.0f MB > 129 MB)" % (npts * 4 / 1e6),
                           "parallelism": "replicas" if world > 1 else "single GPU"},
-               "untiled": untiled, "roofline": roof, "roofline_alu": roof_alu, "roofline_smem": roof_smem,
-               "hbm_bound_16B_untiled_gpts": hbm / 16.0,
-               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+               "value_note": "the autotuner's pick over every compiled one-step and time-tiled pass",
+               "untiled": untiled, "tiled": tiled,
+               "speedup_tiled_over_untiled": (tiled["value"] / untiled["value"]) if tiled and untiled else None,
+               "roofline": roof, "roofline_alu": roof_alu, "roofline_smem": roof_smem,
+               "gradient": grad,
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": rb["kernels"], "clocks": clk.summary("forward"),
+               "clocks_e2e": clk.summary("e2e") if e2e else None,
                "autotune": [[list(t), ms_] for t, ms_ in sorted(tuned, key=lambda c: c[1])[:8]]}
         print(json.dumps(out), flush=True)
-    plan.close()
     if dist is not None:
         dist.destroy_process_group()
 
