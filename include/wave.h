@@ -275,21 +275,55 @@ wave_status wave_sample_noalloc(const int grid[3], const double spacing[3], cons
 
 /* ---- batched shots ---------------------------------------------------------
  * Many independent shots (plans with their own grid, SO, tiling, sources and
- * receivers, as the autotuner chose per shot) advanced together: the whole
- * time loop of every shot is captured into one CUDA graph, each shot on a
- * stream of its own, and replayed with a single graph launch.  The plans
- * must live on one device and stay alive as long as the batch. */
+ * receivers, as the autotuner chose per shot: the per-problem tiling of
+ * Section "Future Work", "Automating time-tiling in Devito") advanced
+ * together.  The plans must live on one device and stay alive as long as the
+ * batch. */
 typedef struct wave_batch_s* wave_batch_t;
 
 wave_status wave_batch_create(wave_batch_t* out, int nplans, const wave_plan_t* plans);
 
+/* Autotune every plan of the batch (wave_autotune with `passes` timed passes
+ * per candidate) over the tilings the persistent batched kernel runs (SO 4
+ * and 8: 512-thread tiles with tensor-memory queues, T = 1, 2 or 3, on x
+ * slabs of 256 planes or the whole grid); plans of SO 16 are tuned over every
+ * candidate. */
+wave_status wave_batch_autotune(wave_batch_t batch, int passes);
+
 /* Forward modelling of every shot from zero fields, the same results as
  * wave_forward per plan (bit-identical).  rec_out: host array of nplans
  * device pointers ([nt_i][nrec_i] each; may be NULL for shots without
- * receivers).  The graph is captured on the first call and again when the
- * rec_out pointers change or a plan's buffers or tiling changed since.
- * Synchronises `stream` (cudaStream_t) and reports device-side timeouts. */
+ * receivers).  When every plan's tiling (and its one-step remainder passes)
+ * has a shape in the persistent batched kernel, all shots run in one
+ * persistent launch: a device work queue lists every (shot, pass, tile) item,
+ * pass level by pass level across the shots; each thread block takes the next
+ * item, waits (bounded, 2 s) until every tile of the shot's previous pass is
+ * done, runs the tile and publishes it.  Otherwise every shot's own pass
+ * launches run on a stream of its own.  Either way the work is captured into
+ * one CUDA graph on the first call, and again when the rec_out pointers
+ * change or a plan's buffers or tiling changed since.  The persistent kernel
+ * reads the pass arguments from one constant-memory array per device, which
+ * the graph writes before the launch: batched forwards of different batches
+ * must not overlap on one device (each call synchronises `stream` before it
+ * returns).  Synchronises `stream` (cudaStream_t) and reports device-side
+ * timeouts (WAVE_ERR_TIMEOUT). */
 wave_status wave_batch_forward(wave_batch_t batch, float* const* rec_out, void* stream);
+
+/* How the last captured forward runs: *persistent = 1 for the persistent
+ * kernel (then *items work items on *blocks thread blocks), 0 for per-shot
+ * launches.  Any output may be NULL. */
+wave_status wave_batch_get_mode(wave_batch_t batch, int* persistent, int* items, int* blocks);
+
+/* Self-test of the persistent kernel's failure detection: runs the batch's
+ * work queue once with shot 0's completion counter withheld (started far
+ * below what its first item waits for), with dependency waits bounded by
+ * limit_ms (0 < limit_ms <= 10000).  The waiting blocks give up, set the
+ * queue's abort word and return; the others stop at their next item.
+ * Returns WAVE_ERR_TIMEOUT when that happened (the expected outcome: the
+ * device stays usable and the next wave_batch_forward recaptures and runs
+ * normally), WAVE_OK if no wait gave up (a defect), WAVE_ERR_STATE if the
+ * batch has no persistent work queue.  The plans' wavefields are scratch. */
+wave_status wave_batch_selftest_withhold(wave_batch_t batch, double limit_ms);
 
 /* FWI gradient of every shot (see wave_gradient), all shots' work --
  * checkpointed forward, residual, adjoint sweep, imaging -- captured in one
@@ -353,6 +387,17 @@ wave_status wave_schedule_verify(const int grid[3], int so, const wave_tiling* t
  * uses r).  Smaller values must be rejected; exposed for tests. */
 wave_status wave_schedule_verify_custom(const int grid[3], int so, const wave_tiling* tiling, int lag,
                                         int halo_per_step);
+
+/* Brute-force legality of the skewed wavefront variant (unroll = 4) on a
+ * tiny grid, with its two inter-tile parameters overridden: the rows of
+ * level n+1 that tile j takes from tile j-1 below it (`exchange_rows`, the
+ * kernel exchanges 2r) and how far ahead of tile j's iteration the published
+ * progress of tile j-1 must be (`wait_lead`, the kernel's wait gives 1).
+ * wave_schedule_verify checks the variant with the kernel's values; smaller
+ * ones must be rejected.  Returns WAVE_OK or WAVE_ERR_ARG with the first
+ * violation in wave_last_error(). */
+wave_status wave_schedule_verify_skew(const int grid[3], int so, const wave_tiling* tiling, int exchange_rows,
+                                      int wait_lead);
 
 /* Brute-force check of the paper's skewed time-tiled loop order in 1D+t
  * (Fig. tiled_skew_snippet / Fig. tiled_256 reduced to one space axis):

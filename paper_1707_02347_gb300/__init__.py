@@ -21,7 +21,7 @@ from . import build as _build
 
 __all__ = [
     "WaveError", "load", "fd_weights", "cfl_limit", "skew_factor", "tiling_check", "schedule_verify",
-    "schedule_verify_custom", "skewed_order_legal", "WavePlan", "WaveBatch", "FWIGradient", "STATUS",
+    "schedule_verify_custom", "schedule_verify_skew", "skewed_order_legal", "WavePlan", "WaveBatch", "FWIGradient", "STATUS",
 ]
 
 STATUS = {0: "WAVE_OK", 1: "WAVE_ERR_ARG", 2: "WAVE_ERR_CFL", 3: "WAVE_ERR_OOM", 4: "WAVE_ERR_CUDA",
@@ -95,11 +95,17 @@ def load(build_if_missing: bool = True):
             "wave_schedule_verify_custom": (st, [_I3, ctypes.c_int, ctypes.POINTER(Tiling), ctypes.c_int,
                                                  ctypes.c_int]),
             "wave_skewed_order_legal": (ctypes.c_int, [ctypes.c_int] * 6),
+            "wave_schedule_verify_skew": (st, [_I3, ctypes.c_int, ctypes.POINTER(Tiling), ctypes.c_int,
+                                               ctypes.c_int]),
             "wave_batch_create": (st, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]),
             "wave_autotune_cached": (st, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "wave_batch_forward": (st, [_VP, ctypes.POINTER(_VP), _VP]),
             "wave_batch_gradient": (st, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _DP, ctypes.c_int, _VP]),
             "wave_batch_destroy": (st, [_VP]),
+            "wave_batch_autotune": (st, [_VP, ctypes.c_int]),
+            "wave_batch_get_mode": (st, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
+            "wave_batch_selftest_withhold": (st, [_VP, ctypes.c_double]),
             "wave_selftest_timeout": (st, [ctypes.c_double]),
             "wave_profile_enable": (st, [_VP, ctypes.c_int]),
             "wave_profile_read": (st, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -161,6 +167,15 @@ def schedule_verify_custom(grid, so: int, tiling, lag: int, halo_per_step: int):
     lib = load()
     rc = lib.wave_schedule_verify_custom(_I3(*grid), int(so), ctypes.byref(_tiling(tiling)), int(lag),
                                          int(halo_per_step))
+    return rc == 0, (lib.wave_last_error() or b"").decode() if rc else ""
+
+
+def schedule_verify_skew(grid, so: int, tiling, exchange_rows: int, wait_lead: int):
+    """(ok, message) of the brute-force check of the skewed wavefront variant
+    with its exchange rows and its progress wait overridden."""
+    lib = load()
+    rc = lib.wave_schedule_verify_skew(_I3(*grid), int(so), ctypes.byref(_tiling(tiling)), int(exchange_rows),
+                                       int(wait_lead))
     return rc == 0, (lib.wave_last_error() or b"").decode() if rc else ""
 
 
@@ -325,9 +340,10 @@ class WavePlan:
 
 
 class WaveBatch:
-    """Several plans (shots) advanced together: one CUDA graph holding every
-    shot's time loop (forward) or whole gradient, one stream per shot, one
-    graph launch per call."""
+    """Several plans (shots) advanced together, one graph launch per call: the
+    forward of every shot in one persistent kernel fed by a device work queue
+    (when every plan's tiling has a shape in it; else one stream per shot),
+    the gradient as every shot's launches, one stream per shot."""
 
     def __init__(self, plans):
         self._lib = load()
@@ -336,6 +352,21 @@ class WaveBatch:
         h = _VP()
         _check(self._lib.wave_batch_create(ctypes.byref(h), len(self.plans), arr))
         self._h = h
+
+    def autotune(self, passes=2):
+        """Tune every plan over the tilings the persistent batched kernel runs."""
+        _check(self._lib.wave_batch_autotune(self._h, int(passes)))
+        return [p.get_tiling() for p in self.plans]
+
+    def mode(self):
+        """(persistent, work items, thread blocks) of the captured forward."""
+        a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(self._lib.wave_batch_get_mode(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return bool(a.value), b.value, c.value
+
+    def selftest_withhold(self, limit_ms=100.0):
+        """Status code of wave_batch_selftest_withhold (5 = WAVE_ERR_TIMEOUT, the expected one)."""
+        return int(self._lib.wave_batch_selftest_withhold(self._h, float(limit_ms)))
 
     def forward(self, recs=None):
         """recs: one CUDA tensor [nt, nrec] per plan (allocated if None)."""

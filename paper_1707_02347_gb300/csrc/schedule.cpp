@@ -147,16 +147,156 @@ std::vector<wave_tiling> tiling_candidates(const int grid[3], int R)
 // Every output point of levels n+T-1 and n+T must be written exactly once,
 // by its owning block, with a valid value.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Brute-force verification of the skewed wavefront variant (T = 2).
+//
+// Model (wave_skew.cuh): tiles of BY rows along y, x slabs and z tiles, taken
+// in wavefront order (y level, slab, z tile).  Tile j computes step 1 (level
+// n+1) on rows [y0, y0 + BY) and step 2 (level n+2) on rows [y0 - r, y0 +
+// BY - r), both over the z columns of its region (z carries an overlapped
+// halo), step k at plane x_k = xbase + i - r k of iteration i (i >= 2 r k).
+// The only values a tile takes from another are level n+1 on the
+// `exchange_rows` rows below y0, produced by tile j-1 of the same slab and z
+// tile; a value tile j-1 produced in its iteration p may be read by tile j
+// in its iteration i only if p <= i + wait_lead - 1 (the kernel waits, before
+// iteration i copies the rows it needs at i+1, until tile j-1 has completed
+// iteration i+1: exchange_rows = 2r, wait_lead = 1).  Rows outside the grid
+// are zero.  Every output point (levels n+1 and n+2, the v form's (u, v))
+// must be written exactly once, by the tile that owns it, with a valid value.
+// ---------------------------------------------------------------------------
+static bool verify_skew_schedule(const int grid[3], int R, const wave_tiling& t, int exchange_rows, int wait_lead,
+                                 std::string* why)
+{
+    PassGeom g;
+    if (!make_geom(grid, R, t, &g, why, false)) return false;
+    if (t.unroll != 4 || t.T != 2) {
+        if (why) *why = "not a skewed wavefront tiling";
+        return false;
+    }
+    const int nx = grid[0], ny = grid[1], nz = grid[2];
+    const int BY = t.by, RY = g.r1y, bcols = g.b_cols;
+    const int nxs = g.nxs;
+    auto in_grid = [&](int x, int y, int z) { return x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz; };
+    auto pidx = [&](int x, int y, int z) { return (static_cast<size_t>(x) * ny + y) * nz + z; };
+    std::vector<int> writes(static_cast<size_t>(nx) * ny * nz, 0);
+    // level n+1 of tile j-1 (same slab and z tile): iteration that produced
+    // it (-1: not produced) and validity, over its box
+    struct Box {
+        int x0 = 0, y0 = 0, z0 = 0, nxb = 0, nyb = 0, nzb = 0;
+        std::vector<int> iter;
+        std::vector<char> ok;
+        size_t at(int x, int y, int z) const
+        {
+            return (static_cast<size_t>(x - x0) * nyb + (y - y0)) * nzb + (z - z0);
+        }
+        bool inside(int x, int y, int z) const
+        {
+            return x >= x0 && x < x0 + nxb && y >= y0 && y < y0 + nyb && z >= z0 && z < z0 + nzb;
+        }
+    };
+    std::vector<Box> prev(static_cast<size_t>(nxs) * g.ntz);  // per (slab, z tile): the tile below
+    for (int tyi = 0; tyi < g.nty; ++tyi)
+        for (int xsi = 0; xsi < nxs; ++xsi)
+            for (int tzi = 0; tzi < g.ntz; ++tzi) {
+                const int y0 = tyi * BY, z0 = tzi * t.bz;
+                const int ylo = y0 - R, zlo = z0 + g.zlead;
+                const int X0 = xsi * g.xc, X1 = std::min(X0 + g.xc, nx);
+                const int NIT = (X1 - X0) + 4 * R, xbase = X0 - 2 * R;
+                Box cur;  // this tile's levels n+1 (index 0) and n+2 (index 1) over its region
+                cur.x0 = xbase - 2 * R;
+                cur.y0 = ylo;
+                cur.z0 = zlo;
+                cur.nxb = NIT + 2 * R;
+                cur.nyb = RY;
+                cur.nzb = bcols;
+                const size_t nb = static_cast<size_t>(cur.nxb) * cur.nyb * cur.nzb;
+                std::vector<int> it1(nb, -1);
+                std::vector<char> ok1(nb, 0), ok2(nb, 0), done2(nb, 0);
+                const Box& below = prev[static_cast<size_t>(xsi) * g.ntz + tzi];
+                // level n+1 at (x, y, z) as read by this tile in iteration i
+                auto lev1 = [&](int x, int y, int z, int i) -> bool {
+                    if (!in_grid(x, y, z)) return true;  // zero ghost
+                    if (y >= y0 && y < y0 + BY) {
+                        if (!cur.inside(x, y, z)) return false;
+                        const size_t a = cur.at(x, y, z);
+                        return it1[a] >= 0 && it1[a] <= i && ok1[a];
+                    }
+                    if (y < y0 && y >= y0 - exchange_rows && tyi > 0) {
+                        if (!below.inside(x, y, z)) return false;
+                        const size_t a = below.at(x, y, z);
+                        return below.iter[a] >= 0 && below.iter[a] <= i + wait_lead - 1 && below.ok[a];
+                    }
+                    return false;  // neither computed here nor exchanged
+                };
+                for (int i = 0; i < NIT; ++i) {
+                    // step 1 at plane x1, rows [y0, y0 + BY): reads the pass input only
+                    if (i >= 2 * R) {
+                        const int x = xbase + i - R;
+                        for (int y = y0; y < y0 + BY; ++y)
+                            for (int z = zlo; z < zlo + bcols; ++z) {
+                                const size_t a = cur.at(x, y, z);
+                                it1[a] = i;
+                                ok1[a] = 1;
+                            }
+                    }
+                    // step 2 at plane x2, rows [y0 - r, y0 + BY - r)
+                    if (i >= 4 * R) {
+                        const int x = xbase + i - 2 * R;
+                        for (int y = y0 - R; y < y0 + BY - R; ++y)
+                            for (int z = zlo; z < zlo + bcols; ++z) {
+                                bool ok = true;
+                                if (in_grid(x, y, z)) {
+                                    for (int j = -R; j <= R && ok; ++j) {
+                                        ok = ok && lev1(x + j, y, z, i);
+                                        ok = ok && lev1(x, y + j, z, i);
+                                        ok = ok && lev1(x, y, z + j, i);
+                                    }
+                                }
+                                const size_t a = cur.at(x, y, z);
+                                ok2[a] = ok;
+                                done2[a] = 1;
+                                // outputs: u^{n+2} and v^{n+3/2} of the owned points
+                                if (x >= X0 && x < X1 && z >= z0 && z < std::min(z0 + t.bz, nz) && y >= 0 &&
+                                    y < ny) {
+                                    if (!ok || !lev1(x, y, z, i)) {
+                                        if (why)
+                                            *why = "tile (" + std::to_string(tyi) + "," + std::to_string(xsi) + "," +
+                                                   std::to_string(tzi) + ") writes an invalid value at (" +
+                                                   std::to_string(x) + "," + std::to_string(y) + "," +
+                                                   std::to_string(z) + ")";
+                                        return false;
+                                    }
+                                    writes[pidx(x, y, z)]++;
+                                }
+                            }
+                    }
+                }
+                Box& keep = prev[static_cast<size_t>(xsi) * g.ntz + tzi];
+                keep = cur;
+                keep.iter = std::move(it1);
+                keep.ok = std::move(ok1);
+            }
+    for (size_t p = 0; p < writes.size(); ++p)
+        if (writes[p] != 1) {
+            if (why) *why = "point " + std::to_string(p) + " written " + std::to_string(writes[p]) + " times";
+            return false;
+        }
+    return true;
+}
+
 static bool verify_schedule(const int grid[3], int R, const wave_tiling& t, int lag, int halo_per_step,
                             std::string* why)
 {
     PassGeom g;
     if (!make_geom(grid, R, t, &g, why, false)) return false;
     if (t.unroll == 4) {
-        // tiles of the skewed variant read each other's values; this model
-        // checks independent overlapped tiles only
-        if (why) *why = "the skewed wavefront variant is not modelled here";
-        return false;
+        // the skewed variant has no lag or halo parameters of its own: its
+        // model checks the exchange between tiles instead
+        if (lag != R || halo_per_step != R) {
+            if (why) *why = "the skewed wavefront variant has no lag or halo parameters";
+            return false;
+        }
+        return verify_skew_schedule(grid, R, t, 2 * R, 1, why);
     }
     const int nx = grid[0], ny = grid[1], nz = grid[2];
     const int T = t.T;
@@ -307,6 +447,16 @@ extern "C" wave_status wave_schedule_verify_custom(const int grid[3], int so, co
     if (!grid || !tiling) return wave::fail(WAVE_ERR_ARG, "wave_schedule_verify_custom: null argument");
     std::string why;
     if (!wave::verify_schedule(grid, so / 2, *tiling, lag, halo_per_step, &why))
+        return wave::fail(WAVE_ERR_ARG, why);
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_schedule_verify_skew(const int grid[3], int so, const wave_tiling* tiling,
+                                                 int exchange_rows, int wait_lead)
+{
+    if (!grid || !tiling) return wave::fail(WAVE_ERR_ARG, "wave_schedule_verify_skew: null argument");
+    std::string why;
+    if (!wave::verify_skew_schedule(grid, so / 2, *tiling, exchange_rows, wait_lead, &why))
         return wave::fail(WAVE_ERR_ARG, why);
     return WAVE_OK;
 }

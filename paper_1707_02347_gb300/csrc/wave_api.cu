@@ -777,8 +777,12 @@ extern "C" wave_status wave_get_sweep_tiling(wave_plan_t p, wave_tiling* t)
     return WAVE_OK;
 }
 
-extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave_tiling* cand, double* ms_per_step,
-                                     int cap, int* ncand)
+namespace {
+
+// wave_autotune over the candidates; batch_only keeps the shapes the
+// persistent batched kernel runs (and their one-step sweep tiling).
+wave_status autotune_impl(wave_plan_t p, int passes, int T_only, bool batch_only, wave_tiling* cand,
+                          double* ms_per_step, int cap, int* ncand)
 {
     if (!p || passes < 1) return fail(WAVE_ERR_ARG, "wave_autotune: bad argument");
     DeviceGuard g(p->dev);
@@ -797,6 +801,11 @@ extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave
         if (T_only > 0 && t.T != T_only) continue;
         PassGeom geom;
         if (!make_geom(p->n, p->R, t, &geom, nullptr)) continue;
+        // batch tilings: the persistent kernel's shapes, on slabs of 256 planes (or all of x), so that
+        // the pipeline fill of a work item (2 r T planes) costs little beside its slab
+        if (batch_only && (batch_shape_index(p->R, geom.T, geom.qz, geom.r1y, t.unroll) < 0 ||
+                           t.xc != std::min(256, p->n[0])))
+            continue;
         Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
         auto one = [&](int n0) -> wave_status { return step_pass(p, geom, &f, none, nullptr, nullptr, n0); };
         wave_status s = one(0);
@@ -839,6 +848,14 @@ extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave
         }
     }
     return apply_tiling(p, best_t);
+}
+
+}  // namespace
+
+extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave_tiling* cand, double* ms_per_step,
+                                     int cap, int* ncand)
+{
+    return autotune_impl(p, passes, T_only, false, cand, ms_per_step, cap, ncand);
 }
 
 namespace {
@@ -1224,6 +1241,20 @@ struct wave_batch_s {
     std::vector<float*> ggrad;
     std::vector<int> gK;
     std::vector<unsigned long long> ggens;
+    // persistent kernel of the forward graph: descriptors, tensor maps and
+    // items of the work queue, and its counters [next, abort, err, pad,
+    // done[nplans]] (device memory, built before the capture)
+    bool persistent = false;
+    BatchDesc* pdesc = nullptr;
+    PassArgs* pargs = nullptr;
+    CUtensorMap* pmaps = nullptr;
+    size_t pdesc_cap = 0, pargs_cap = 0, pmaps_cap = 0;
+    int pndesc = 0;
+    int4* pitems = nullptr;
+    size_t pitems_cap = 0;
+    int pnitems = 0;
+    int* pctl = nullptr;
+    int pblocks = 0;
 };
 
 namespace {
@@ -1287,8 +1318,9 @@ wave_status batch_capture_with(wave_batch_t b, cudaGraph_t* graph, cudaGraphExec
     return WAVE_OK;
 }
 
-// Launch a captured graph, wait, and check every shot's error word.
-wave_status batch_run(wave_batch_t b, cudaGraphExec_t exec, cudaStream_t st)
+// Launch a captured graph, wait, and check every shot's error word (and the
+// persistent kernel's, when the graph runs it).
+wave_status batch_run(wave_batch_t b, cudaGraphExec_t exec, cudaStream_t st, bool persistent = false)
 {
     for (auto* p : b->plans) CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
     CK(cudaGraphLaunch(exec, st));
@@ -1296,6 +1328,201 @@ wave_status batch_run(wave_batch_t b, cudaGraphExec_t exec, cudaStream_t st)
     for (auto* p : b->plans) {
         CK(cudaMemcpy(p->err_host, p->err, sizeof(int), cudaMemcpyDeviceToHost));
         if (*p->err_host) return fail(WAVE_ERR_TIMEOUT, "a bounded device-side wait gave up in a batched shot");
+    }
+    if (persistent) {
+        int err = 0;
+        CK(cudaMemcpy(&err, b->pctl + 2, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) return fail(WAVE_ERR_TIMEOUT, err & 2 ? "a work item of the persistent batch waited too long for its shot's previous pass"
+                                                       : "a bounded device-side wait gave up in the persistent batch");
+    }
+    return WAVE_OK;
+}
+
+// ---- the persistent kernel ---------------------------------------------
+
+// The one-step geometry a plan's remainder passes use in the persistent
+// kernel: its own one-step sweep tiling when the kernel has that shape, else
+// the kernel's one-step shape (every one-step variant computes the same
+// bits).  False if the plan's passes have no shape in the kernel.
+bool batch_geometry(wave_plan_t p, PassGeom* g1)
+{
+    if (p->R != 2 && p->R != 4) return false;
+    const PassGeom& g = p->geom;
+    if (batch_shape_index(p->R, g.T, g.qz, g.r1y, p->tiling.unroll) < 0) return false;
+    if (batch_shape_index(p->R, p->geom1.T, p->geom1.qz, p->geom1.r1y, p->tiling1.unroll) >= 0) {
+        *g1 = p->geom1;
+        return true;
+    }
+    const wave_tiling t1{1, 32, 64, p->geom1.xc > 0 ? p->geom1.xc : std::min(p->n[0], 64), 2};
+    return make_geom(p->n, p->R, t1, g1, nullptr) && batch_shape_index(p->R, 1, g1->qz, g1->r1y, 2) >= 0;
+}
+
+template <class T>
+wave_status grow(T** ptr, size_t* cap, size_t n)
+{
+    if (n <= *cap) return WAVE_OK;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    CK(cudaMalloc(reinterpret_cast<void**>(ptr), n * sizeof(T)));
+    *cap = n;
+    return WAVE_OK;
+}
+
+// Build the work queue of a forward run of every plan from zero fields: the
+// passes of each plan exactly as advance() runs them (tiled passes, then
+// one-step passes), one descriptor per distinct (plan, geometry, buffers),
+// and the items pass level by pass level across the plans.  *ok = false (and
+// nothing built) when some plan has no shape in the persistent kernel.
+wave_status batch_persistent_build(wave_batch_t b, bool* ok)
+{
+    *ok = false;
+    const size_t n = b->plans.size();
+    std::vector<PassGeom> g1(n);
+    for (size_t i = 0; i < n; ++i)
+        if (!batch_geometry(b->plans[i], &g1[i])) return WAVE_OK;
+    struct Level {
+        const PassGeom* g;
+        float *u, *v, *ou, *ov;
+        int n0;
+    };
+    std::vector<std::vector<Level>> levels(n);
+    for (size_t i = 0; i < n; ++i) {
+        wave_plan_t p = b->plans[i];
+        Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
+        int t = 0;
+        if (p->geom.T > 1) {
+            while (t + p->geom.T <= p->nt) {
+                levels[i].push_back({&p->geom, f.u, f.v, f.f0, f.f1, t});
+                std::swap(f.u, f.f0);
+                std::swap(f.v, f.f1);
+                t += p->geom.T;
+            }
+        }
+        const PassGeom* gr = p->geom.T == 1 ? &p->geom : &g1[i];
+        while (t < p->nt) {
+            levels[i].push_back({gr, f.u, f.v, f.f0, f.v, t});
+            std::swap(f.u, f.f0);
+            t += 1;
+        }
+    }
+    // descriptors, their pass arguments and tensor maps
+    std::vector<BatchDesc> descs;
+    std::vector<PassArgs> args;
+    std::vector<CUtensorMap> maps;
+    std::vector<std::vector<int>> dlev(n);
+    std::map<std::tuple<size_t, const PassGeom*, float*, float*, float*>, int> seen;
+    for (size_t i = 0; i < n; ++i) {
+        wave_plan_t p = b->plans[i];
+        float* slots = nullptr;
+        if (p->fwd.nrec > 0 && p->fwd.ntaps > 0) {
+            wave_status st = ensure_slots(p, static_cast<size_t>(p->nt) * p->fwd.ntaps);
+            if (st) return st;
+            slots = p->slots;
+        }
+        for (const Level& lv : levels[i]) {
+            auto key = std::make_tuple(i, lv.g, lv.u, lv.v, lv.ou);
+            auto it = seen.find(key);
+            if (it == seen.end()) {
+                const CUtensorMap* mA = get_map(p, lv.u, lv.g->a_rows, lv.g->a_cols);
+                const CUtensorMap* mV = get_map(p, lv.v, lv.g->b_rows, lv.g->b_cols);
+                const CUtensorMap* mK = get_map(p, p->kap, lv.g->b_rows, lv.g->b_cols);
+                if (!mA || !mV || !mK) return fail(WAVE_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+                PassArgs a = base_args(p, *lv.g, p->fwd, p->wavelet, slots);
+                a.out_u = lv.ou;
+                a.out_v = lv.ov;
+                a.err = b->pctl + 2;
+                BatchDesc d;
+                d.shot = static_cast<int>(i);
+                d.shape = batch_shape_index(p->R, lv.g->T, lv.g->qz, lv.g->r1y, 2);
+                it = seen.emplace(key, static_cast<int>(descs.size())).first;
+                descs.push_back(d);
+                args.push_back(a);
+                maps.push_back(*mA);
+                maps.push_back(*mV);
+                maps.push_back(*mK);
+            }
+            dlev[i].push_back(it->second);
+        }
+    }
+    // items: pass level by pass level, every plan's tiles of that level in turn
+    std::vector<int4> items;
+    std::vector<int> cum(n, 0);
+    for (size_t L = 0;; ++L) {
+        bool any = false;
+        for (size_t i = 0; i < n; ++i) {
+            if (L >= levels[i].size()) continue;
+            any = true;
+            const Level& lv = levels[i][L];
+            for (long long t = 0; t < lv.g->blocks; ++t) items.push_back(make_int4(dlev[i][L], static_cast<int>(t), cum[i], lv.n0));
+            cum[i] += static_cast<int>(lv.g->blocks);
+        }
+        if (!any) break;
+    }
+    // the persistent kernel reads the arguments from a constant array of kMaxBatchArgs entries
+    if (descs.size() > static_cast<size_t>(kMaxBatchArgs)) return WAVE_OK;
+    wave_status st = grow(&b->pdesc, &b->pdesc_cap, std::max<size_t>(descs.size(), 1));
+    if (st) return st;
+    st = grow(&b->pargs, &b->pargs_cap, std::max<size_t>(args.size(), 1));
+    if (st) return st;
+    st = grow(&b->pmaps, &b->pmaps_cap, std::max<size_t>(3 * descs.size(), 3));
+    if (st) return st;
+    st = grow(&b->pitems, &b->pitems_cap, std::max<size_t>(items.size(), 1));
+    if (st) return st;
+    if (!descs.empty()) {
+        CK(cudaMemcpy(b->pdesc, descs.data(), descs.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b->pargs, args.data(), args.size() * sizeof(PassArgs), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b->pmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    }
+    if (!items.empty())
+        CK(cudaMemcpy(b->pitems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    b->pnitems = static_cast<int>(items.size());
+    b->pndesc = static_cast<int>(descs.size());
+    b->pblocks = static_cast<int>(std::min<long long>(b->plans[0]->sm_count, std::max<long long>(1, b->pnitems)));
+    *ok = true;
+    return WAVE_OK;
+}
+
+// bound on a work item's wait for its shot's previous pass (as on every wait of the pass kernels)
+constexpr unsigned long long kBatchWaitLimitNs = 2000000000ull;
+
+BatchQueue batch_queue(wave_batch_t b, unsigned long long limit_ns)
+{
+    BatchQueue q;
+    q.desc = b->pdesc;
+    q.maps = b->pmaps;
+    q.items = b->pitems;
+    q.nitems = b->pnitems;
+    q.next = b->pctl;
+    q.abort = b->pctl + 1;
+    q.err = b->pctl + 2;
+    q.done = b->pctl + 4;
+    q.limit_ns = limit_ns;
+    return q;
+}
+
+// Stream work of the persistent forward on stream st: zero fields and
+// counters, the persistent kernel, then every plan's traces from its slots.
+wave_status batch_persistent_enqueue(wave_batch_t b, float* const* rec_out, cudaStream_t st)
+{
+    const size_t n = b->plans.size();
+    for (size_t i = 0; i < n; ++i) {
+        wave_plan_t p = b->plans[i];
+        CK(cudaMemsetAsync(p->buf[0], 0, p->npad * 4, st));
+        CK(cudaMemsetAsync(p->buf[1], 0, p->npad * 4, st));
+    }
+    CK(cudaMemsetAsync(b->pctl, 0, (4 + n) * sizeof(int), st));
+    CK(batch_copy_args(b->pargs, b->pndesc, st));
+    if (b->pnitems > 0) CK(launch_batch(batch_queue(b, kBatchWaitLimitNs), b->pblocks, st));
+    for (size_t i = 0; i < n; ++i) {
+        wave_plan_t p = b->plans[i];
+        p->launches++;
+        if (p->fwd.nrec == 0 || p->nt == 0) continue;
+        if (p->fwd.ntaps > 0)
+            CKL(launch_rec_reduce(p->slots, p->fwd.rec_tptr, p->fwd.rec_tw, rec_out[i], p->nt, p->fwd.nrec,
+                                  p->fwd.ntaps, st));
+        else
+            CK(cudaMemsetAsync(rec_out[i], 0, static_cast<size_t>(p->nt) * p->fwd.nrec * 4, st));
     }
     return WAVE_OK;
 }
@@ -1316,10 +1543,31 @@ wave_status batch_capture(wave_batch_t b, float* const* rec_out)
         }
     }
     batch_release_graph(b);
-    wave_status s = batch_capture_with(b, &b->graph, &b->exec, [&](size_t i) {
-        return forward_impl(b->plans[i], nullptr, rec_out ? rec_out[i] : nullptr, nullptr);
-    });
+    // one persistent launch for every shot when each plan's passes have a
+    // shape in the persistent kernel; otherwise every shot's own launches on
+    // a stream of its own
+    bool ok = false;
+    wave_status s = batch_persistent_build(b, &ok);
     if (s) return s;
+    b->persistent = ok;
+    if (ok) {
+        CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        s = batch_persistent_enqueue(b, rec_out, b->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (s) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return check_cuda("cudaStreamEndCapture", e);
+        b->graph = g;
+        CK(cudaGraphInstantiate(&b->exec, g, 0));
+    } else {
+        s = batch_capture_with(b, &b->graph, &b->exec, [&](size_t i) {
+            return forward_impl(b->plans[i], nullptr, rec_out ? rec_out[i] : nullptr, nullptr);
+        });
+        if (s) return s;
+    }
     b->recs.assign(rec_out ? rec_out : nullptr, rec_out ? rec_out + n : nullptr);
     b->gens = batch_gens(b);
     return WAVE_OK;
@@ -1351,6 +1599,7 @@ extern "C" wave_status wave_batch_create(wave_batch_t* out, int nplans, const wa
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) b->events.push_back(ev);
     }
+    if (e == cudaSuccess) e = cudaMalloc(&b->pctl, (4 + static_cast<size_t>(nplans)) * sizeof(int));
     if (e != cudaSuccess) {
         wave_batch_destroy(b);
         return check_cuda("wave_batch_create", e);
@@ -1370,7 +1619,55 @@ extern "C" wave_status wave_batch_forward(wave_batch_t b, float* const* rec_out,
         wave_status s = batch_capture(b, rec_out);
         if (s) return s;
     }
-    return batch_run(b, b->exec, static_cast<cudaStream_t>(stream));
+    return batch_run(b, b->exec, static_cast<cudaStream_t>(stream), b->persistent);
+}
+
+extern "C" wave_status wave_batch_autotune(wave_batch_t b, int passes)
+{
+    if (!b || passes < 1) return fail(WAVE_ERR_ARG, "wave_batch_autotune: bad argument");
+    DeviceGuard g(b->dev);
+    for (auto* p : b->plans) {
+        int count = 0;
+        wave_status s = autotune_impl(p, passes, 0, p->R == 2 || p->R == 4, nullptr, nullptr, 0, &count);
+        if (s) return s;
+    }
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_batch_get_mode(wave_batch_t b, int* persistent, int* items, int* blocks)
+{
+    if (!b) return fail(WAVE_ERR_ARG, "wave_batch_get_mode: null batch");
+    if (persistent) *persistent = b->persistent ? 1 : 0;
+    if (items) *items = b->persistent ? b->pnitems : 0;
+    if (blocks) *blocks = b->persistent ? b->pblocks : 0;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_batch_selftest_withhold(wave_batch_t b, double limit_ms)
+{
+    if (!b || !(limit_ms > 0.0) || limit_ms > 10000.0)
+        return fail(WAVE_ERR_ARG, "wave_batch_selftest_withhold: limit_ms must be in (0, 10000]");
+    DeviceGuard g(b->dev);
+    bool ok = false;
+    wave_status s = batch_persistent_build(b, &ok);
+    if (s) return s;
+    if (!ok || b->pnitems == 0) return fail(WAVE_ERR_STATE, "wave_batch_selftest_withhold: the batch has no persistent work queue");
+    // the graph (if any) was captured with the previous queue: capture again on the next forward
+    batch_release_graph(b);
+    b->gens.clear();
+    const size_t n = b->plans.size();
+    cudaStream_t st = b->cap;
+    CK(cudaMemsetAsync(b->pctl, 0, (4 + n) * sizeof(int), st));
+    // shot 0's counter starts far below any item's need: its first item waits and gives up
+    const int withheld = -(1 << 30);
+    CK(cudaMemcpyAsync(b->pctl + 4, &withheld, sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(batch_copy_args(b->pargs, b->pndesc, st));
+    CK(launch_batch(batch_queue(b, static_cast<unsigned long long>(limit_ms * 1e6)), b->pblocks, st));
+    CK(cudaStreamSynchronize(st));
+    int err = 0;
+    CK(cudaMemcpy(&err, b->pctl + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & 2) return fail(WAVE_ERR_TIMEOUT, "a withheld dependency made a work item give up, as intended");
+    return WAVE_OK;
 }
 
 extern "C" wave_status wave_batch_gradient(wave_batch_t b, const float* const* d_obs, float* const* grad_m,
@@ -1418,6 +1715,11 @@ extern "C" wave_status wave_batch_destroy(wave_batch_t b)
     if (b->cap) cudaStreamSynchronize(b->cap);
     batch_release_graph(b);
     batch_release_ggraph(b);
+    cudaFree(b->pdesc);
+    cudaFree(b->pargs);
+    cudaFree(b->pmaps);
+    cudaFree(b->pitems);
+    cudaFree(b->pctl);
     for (auto s : b->streams) cudaStreamDestroy(s);
     for (auto e : b->events) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);

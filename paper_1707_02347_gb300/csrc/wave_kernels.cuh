@@ -72,6 +72,38 @@ struct PassShape {
 const PassShape* pass_shapes(int* count);
 const PassShape* find_pass_shape(int R, int T, int qz, int ry, int unroll);
 
+// Persistent kernel of batched shots (wave_batch.cu).  One descriptor per
+// (shot, pass kind): the shot's index and the index of its compiled batch
+// shape; its pass arguments (n0 set per item) are entry d of the kernel's
+// constant array (batch_copy_args), its three tensor maps (u^n with the
+// stencil halo, v^{n-1/2}, kappa) maps[3 d .. 3 d + 2].  Items are int4
+// {descriptor, tile, tiles of the shot that must be done first, n0}, in
+// queue order.
+constexpr int kMaxBatchArgs = 112;
+struct BatchDesc {
+    int shot;
+    int shape;
+};
+struct BatchQueue {
+    const BatchDesc* desc;
+    const CUtensorMap* maps;  // 64-byte aligned
+    const int4* items;
+    int nitems;
+    int* next;                // work counter (starts at 0)
+    int* done;                // finished tiles per shot (start at 0)
+    int* abort;               // set when a dependency wait gave up
+    int* err;                 // bit 0: a tile's TMA wait gave up; bit 1: a dependency wait gave up
+    unsigned long long limit_ns;  // bound on a dependency wait
+};
+// Index of the compiled batch shape (radius, T, z quads per row, rows,
+// variant) or -1; the dynamic shared memory of the kernel; its launch.
+int batch_shape_index(int R, int T, int qz, int ry, int unroll);
+size_t batch_smem_bytes();
+// Copy n <= kMaxBatchArgs pass arguments (device memory) into the constant
+// array the persistent kernel reads; stream-ordered (capturable).
+cudaError_t batch_copy_args(const PassArgs* dev_args, int n, cudaStream_t st);
+cudaError_t launch_batch(const BatchQueue& q, int blocks, cudaStream_t st);
+
 // Elementwise helpers.
 cudaError_t launch_kappa(const float* m, float* kap, int nx, int ny, int nz, int nzp, float dt2, cudaStream_t st);
 cudaError_t launch_pad_copy(const float* src, float* dst, int nx, int ny, int nz, int nzp, cudaStream_t st);

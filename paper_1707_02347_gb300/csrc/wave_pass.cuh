@@ -494,10 +494,23 @@ constexpr int min_blocks()
                                      : 1;
 }
 
+__device__ __forceinline__ void mbar_inval(uint32_t bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// One output tile (thread block `blk` of the pass's grid) of a pass: the
+// body of pass_kernel, and the work item of the persistent batched kernel.
+// mapA, mapV, mapK: tensor maps (kernel parameters or global memory); a:
+// the pass arguments (kernel parameter or constant memory), with n0 the time
+// level at the start of the pass (in place of a.n0); tmem_base: the block's
+// tensor-memory allocation (QM = 2; at least TmemGeo::COLS columns); reuse:
+// the block runs another tile after this one, so the tile's mbarriers are
+// invalidated at its end.
 template <int R, int T, int QZ, int RY, int QM>
-__global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
-    pass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
-                const __grid_constant__ CUtensorMap mapK, const PassArgs a)
+__device__ __forceinline__ void pass_tile(const CUtensorMap* mapA, const CUtensorMap* mapV, const CUtensorMap* mapK,
+                                          const PassArgs& a, int n0, long long blk, unsigned char* smem,
+                                          uint32_t tmem_base, bool reuse)
 {
     using C = Cfg<R, T>;
     using G = Geo<R, T, QZ, RY>;
@@ -508,10 +521,8 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
     constexpr int afl = G::AFL, bfl = G::BFL, pitch = G::A_COLS, NTHR = G::NTHR;
     constexpr int R2 = 2 * R;
     constexpr uint32_t hdr = (8u * (NA + NB) + 8u + 127u) & ~127u;
-    extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     volatile int* s_abort = reinterpret_cast<volatile int*>(smem + 8 * (NA + NB));
-    volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + 8 * (NA + NB) + 4);
     // disjoint regions: the TMA rings, the published planes, the increment ring
     float* __restrict__ ringA = reinterpret_cast<float*>(smem + hdr);
     float* __restrict__ ringB = ringA + NA * afl;
@@ -521,7 +532,6 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
     constexpr uint32_t txB = static_cast<uint32_t>(2 * G::B_ROWS * G::B_COLS * 4);
 
     // thread block -> tile (z fastest, then y, then x slab)
-    long long blk = blockIdx.x;
     const int tzi = static_cast<int>(blk % a.ntz);
     blk /= a.ntz;
     const int tyi = static_cast<int>(blk % a.nty);
@@ -592,27 +602,18 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
         }
     }
 
-    if constexpr (TQ) {
-        // warp 0 allocates the block's tensor memory (all 32 threads)
-        __syncwarp();
-        if (tid < 32) {
-            tmem_alloc(smem_u32(const_cast<uint32_t*>(s_tmem)), TG::COLS);
-            tmem_relinquish();
-        }
-    }
     if (tid == 0) {
         for (int s = 0; s < NA + NB; ++s) mbar_init(smem_u32(&bars[s]), 1);
         *s_abort = 0;
         fence_mbar_init();
     }
-    if constexpr (TQ) tmem_fence_before();
     __syncthreads();
     // this warp's columns: lane quarter (warp % 4), column block (warp / 4)
     uint32_t twarp = 0;
     if constexpr (TQ) {
-        tmem_fence_after();
         const int warp = tid >> 5;
-        twarp = *s_tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + static_cast<uint32_t>((warp >> 2) * TG::CPW);
+        twarp = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                static_cast<uint32_t>((warp >> 2) * TG::CPW);
     }
     // column of slot s (0 .. 4r - 1) of the ring of step k
     auto tcol = [&](int k, int s) { return twarp + static_cast<uint32_t>(k * TG::CPS + 4 * s); };
@@ -621,12 +622,12 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
         const int x0 = xbase + j;
         const uint32_t ba = smem_u32(&bars[j % NA]);
         mbar_expect_tx(ba, txA);
-        tma_load3(smem_u32(ringA + (j % NA) * afl), &mapA, ba, zlo - ZH, ylo - R, x0);
+        tma_load3(smem_u32(ringA + (j % NA) * afl), mapA, ba, zlo - ZH, ylo - R, x0);
         const uint32_t bb = smem_u32(&bars[NA + j % NB]);
         float* bs = ringB + (j % NB) * 2 * bfl;
         mbar_expect_tx(bb, txB);
-        tma_load3(smem_u32(bs), &mapV, bb, zlo, ylo, x0 - R);
-        tma_load3(smem_u32(bs + bfl), &mapK, bb, zlo, ylo, x0 - R);
+        tma_load3(smem_u32(bs), mapV, bb, zlo, ylo, x0 - R);
+        tma_load3(smem_u32(bs + bfl), mapK, bb, zlo, ylo, x0 - R);
     };
     int issued = 0;
     if (tid == 0) {
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
                             const int4 e = a.src_ent[c];
                             if (e.x != xk) break;
                             const float w = __int_as_float(e.w);
-                            const float qv = a.wavelet[static_cast<long long>(a.n0 + k) * a.nsrc + e.z];
+                            const float qv = a.wavelet[static_cast<long long>(n0 + k) * a.nsrc + e.z];
                             if (e.y == 0) L.x = __fmaf_rn(w, qv, L.x);
                             else if (e.y == 1) L.y = __fmaf_rn(w, qv, L.y);
                             else if (e.y == 2) L.z = __fmaf_rn(w, qv, L.z);
@@ -794,7 +795,7 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
                             const int2 e = a.rec_ent[c];
                             if (e.x != xk) break;
                             if (xk < X1)
-                                a.slots[static_cast<long long>(a.n0 + k - a.slot_row0) * a.ntaps + (e.y >> 2)] =
+                                a.slots[static_cast<long long>(n0 + k - a.slot_row0) * a.ntaps + (e.y >> 2)] =
                                     lane_of(u, e.y & 3);
                             ++c;
                         }
@@ -855,12 +856,41 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
         for (; i < NIT && !abort; ++i) body(i, std::integral_constant<int, T>{}, std::true_type{}, NoRot{});
     }
     if constexpr (TQ) {
-        // every warp is done with the tensor memory before warp 0 frees it
+        // every warp is done with the tensor memory before it is freed or reused
         tmem_wait_st();
+        tmem_fence_before();
+    }
+    if (TQ || reuse) __syncthreads();
+    if constexpr (TQ) tmem_fence_after();
+    if (reuse && tid == 0)
+        for (int s = 0; s < NA + NB; ++s) mbar_inval(smem_u32(&bars[s]));
+}
+
+template <int R, int T, int QZ, int RY, int QM>
+__global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
+    pass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
+                const __grid_constant__ CUtensorMap mapK, const PassArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    using TG = TmemGeo<R, T, QZ, RY>;
+    constexpr bool TQ = QM == 2;
+    // the tensor-memory address lives in the header word after the abort flag
+    volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + 8 * (Cfg<R, T>::NA + Cfg<R, T>::NB) + 4);
+    uint32_t tbase = 0;
+    if constexpr (TQ) {
+        // warp 0 allocates the block's tensor memory (all 32 threads)
+        if (threadIdx.x < 32) {
+            tmem_alloc(smem_u32(const_cast<uint32_t*>(s_tmem)), TG::COLS);
+            tmem_relinquish();
+        }
         tmem_fence_before();
         __syncthreads();
         tmem_fence_after();
-        if (tid < 32) tmem_dealloc(*s_tmem, TG::COLS);
+        tbase = *s_tmem;
+    }
+    pass_tile<R, T, QZ, RY, QM>(&mapA, &mapV, &mapK, a, a.n0, blockIdx.x, smem, tbase, false);
+    if constexpr (TQ) {
+        if (threadIdx.x < 32) tmem_dealloc(tbase, TG::COLS);
     }
 }
 

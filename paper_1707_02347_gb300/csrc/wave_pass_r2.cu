@@ -25,12 +25,14 @@ const PassShape* pass_shapes_r2(int* n)
         WAVE_SHAPE(1, 16, 16, 1),
         WAVE_SHAPE(1, 16, 16, 2),
         WAVE_SHAPE(1, 16, 8, 2),
+        WAVE_SHAPE(1, 16, 32, 2),
         WAVE_SHAPE(2, 16, 16, 0),
         WAVE_SHAPE(2, 8, 32, 0),
         WAVE_SHAPE(2, 16, 24, 0),
         WAVE_SHAPE(2, 16, 16, 1),
         WAVE_SHAPE(2, 16, 24, 2),
         WAVE_SHAPE(2, 16, 32, 2),
+        WAVE_SHAPE(2, 8, 64, 2),
         WAVE_SHAPE(3, 8, 32, 0),
         WAVE_SHAPE(3, 16, 24, 0),
         WAVE_SHAPE(3, 8, 32, 1),

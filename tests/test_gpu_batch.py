@@ -177,3 +177,111 @@ def test_full_size_batched_shots(oracle):
     batch.close()
     for p in plans:
         p.close()
+
+
+# tilings of the persistent batched kernel (512-thread tiles, tensor-memory
+# queues): SO4 and SO8, T = 1, 2, 3, both tile orientations
+_PERSISTENT = {4: [(1, 32, 64, 32, 2), (2, 28, 56, 32, 2), (2, 60, 24, 32, 2), (3, 24, 56, 32, 2)],
+               8: [(1, 32, 64, 32, 2), (2, 24, 56, 32, 2), (2, 56, 24, 32, 2)]}
+
+
+def test_persistent_batch_matches_single_plans_and_recovers_from_timeout(oracle):
+    """Every shot's tiling has a shape in the persistent kernel, so the batch
+    runs as one persistent launch fed by the device work queue: its traces
+    equal each plan's own wave_forward bit for bit (nt not a multiple of T:
+    the remainder passes run one-step tiles in the same queue) and match the
+    FP64 oracle.  Then a dependency is withheld on the host side: the waiting
+    work items give up after 50 ms with WAVE_ERR_TIMEOUT, and the next
+    batched forward runs normally with the same bits."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1707_02347_gb300 as W
+
+    W.load()
+    dev = torch.device("cuda")
+    shots = _shots(7, 17)
+    plans = []
+    for i, w in enumerate(shots):
+        m = torch.from_numpy(np.ascontiguousarray(w.m)).to(dev)
+        opts = _PERSISTENT[w.so]
+        p = W.WavePlan(w.shape, w.spacing, w.so, w.dt, w.nt, m, sponge_width=w.sponge_width, vmax=w.vmax,
+                       tiling=opts[(i // 2) % len(opts)])
+        p.set_sources(w.src_xyz, torch.from_numpy(w.wavelet.astype(np.float32)).to(dev))
+        p.set_receivers(w.rec_xyz)
+        plans.append(p)
+    assert any(w.nt % p.get_tiling()[0] for w, p in zip(shots, plans))  # some remainder passes
+    single = []
+    for p in plans:
+        rec, _ = p.forward()
+        single.append(rec.clone())
+    batch = W.WaveBatch(plans)
+    for rep in range(2):
+        recs = batch.forward()
+        torch.cuda.synchronize()
+        persistent, items, blocks = batch.mode()
+        assert persistent and items > 0 and blocks > 0
+        for a, b in zip(recs, single):
+            assert torch.equal(a, b)
+    w = shots[1]
+    ref, _, _ = oracle.forward(w.shape, w.spacing, w.so, w.dt, w.nt, w.m.astype(np.float64), src_xyz=w.src_xyz,
+                               wavelet=w.wavelet.astype(np.float32).astype(np.float64), rec_xyz=w.rec_xyz,
+                               sponge_width=w.sponge_width, sponge_faces=w.sponge_faces, vmax=w.vmax)
+    assert_close(recs[1].cpu().numpy(), ref, 1e-5, "persistent batch traces")
+    # failure detection: a withheld dependency times out, the device stays usable
+    assert batch.selftest_withhold(50.0) == 5  # WAVE_ERR_TIMEOUT
+    recs = batch.forward()
+    torch.cuda.synchronize()
+    assert batch.mode()[0]
+    for a, b in zip(recs, single):
+        assert torch.equal(a, b)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_full_size_persistent_batch_autotuned(oracle):
+    """Four shots of the 24-shot workload at their full sizes (the same draws
+    of seed 5, 600 steps), each autotuned over the persistent kernel's
+    tilings: one persistent launch gives every plan's own wave_forward traces
+    bit for bit, and the smallest shot matches the FP64 oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1707_02347_gb300 as W
+    from paper_1707_02347_gb300 import inputs
+
+    W.load()
+    dev = torch.device("cuda")
+    nt = 600
+    rng = np.random.default_rng(5)
+    draws = []
+    for s in range(24):
+        shape = (int(rng.integers(128, 321)), int(rng.integers(128, 321)), int(rng.integers(128, 257)))
+        draws.append((shape, 4 if s % 2 == 0 else 8, float(rng.uniform(8.0, 15.0))))
+    plans, works = [], []
+    for s in (0, 2, 3, 21):
+        shape, so, f = draws[s]
+        w = inputs.layered_forward(shape, so, nt, seed=500 + s, f=f, h=10.0, sponge_width=10, nrec_line=64)
+        m = torch.from_numpy(np.ascontiguousarray(w.m)).to(dev)
+        p = W.WavePlan(w.shape, w.spacing, so, w.dt, nt, m, sponge_width=w.sponge_width, vmax=w.vmax)
+        p.set_sources(w.src_xyz, torch.from_numpy(w.wavelet.astype(np.float32)).to(dev))
+        p.set_receivers(w.rec_xyz)
+        plans.append(p)
+        works.append(w)
+    batch = W.WaveBatch(plans)
+    tilings = batch.autotune(passes=1)
+    assert all(t[4] == 2 for t in tilings), tilings
+    single = [p.forward()[0].clone() for p in plans]
+    recs = batch.forward()
+    torch.cuda.synchronize()
+    assert batch.mode()[0]
+    for r, r1 in zip(recs, single):
+        assert torch.equal(r, r1)
+    k = 2  # draw 3: 206 x 128 x 134, SO8
+    w = works[k]
+    rec_o, _, _ = oracle.forward(w.shape, w.spacing, w.so, w.dt, nt, w.m.astype(np.float64), src_xyz=w.src_xyz,
+                                 wavelet=w.wavelet.astype(np.float32).astype(np.float64), rec_xyz=w.rec_xyz,
+                                 sponge_width=w.sponge_width, sponge_faces=w.sponge_faces, vmax=w.vmax)
+    assert_close(recs[k].cpu().numpy(), rec_o, 1e-5, "smallest full-size shot, persistent")
+    batch.close()
+    for p in plans:
+        p.close()

@@ -159,8 +159,28 @@ def test_warp_specialised_schedule_is_legal(W, so, tiling):
     assert ok, msg
 
 
-def test_schedule_verifier_declines_skewed_variant(W):
-    # the brute-force verifier models independent (overlapped) tiles only; the
-    # skewed variant is checked bit for bit against the one-step kernel on the GPU
-    ok, why = W.schedule_verify((40, 36, 44), 8, (2, 28, 56, 16, 4))
-    assert not ok and "skewed" in why
+@pytest.mark.parametrize("so,grid,tiling", [
+    (8, (40, 90, 44), (2, 28, 56, 16, 4)),  # several y levels and z tiles, two slabs
+    (8, (25, 130, 70), (2, 60, 24, 9, 4)),  # the other compiled shape, three slabs
+    (4, (31, 95, 30), (2, 30, 56, 11, 4)),
+    (8, (20, 17, 9), (2, 28, 56, 20, 4)),  # one y tile taller than the grid
+])
+def test_skewed_wavefront_schedule_is_legal(W, so, grid, tiling):
+    """The skewed wavefront variant in the brute-force model: every step-2
+    value reads either its own tile's step-1 values or the 2r rows tile j-1
+    exchanged, published no later than the iteration that reads them."""
+    ok, msg = W.schedule_verify(grid, so, tiling)
+    assert ok, msg
+    ok, msg = W.schedule_verify_skew(grid, so, tiling, so, 1)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("so,grid,tiling", [(8, (40, 90, 44), (2, 28, 56, 16, 4)), (4, (31, 95, 30), (2, 30, 56, 11, 4))])
+def test_skewed_wavefront_short_exchange_or_missing_wait_is_rejected(W, so, grid, tiling):
+    r = so // 2
+    # fewer than 2r exchanged rows: the lowest step-2 rows lack a y neighbour
+    ok, why = W.schedule_verify_skew(grid, so, tiling, 2 * r - 1, 1)
+    assert not ok and "invalid" in why
+    # no progress wait: tile j would read a plane tile j-1 has not published yet
+    ok, why = W.schedule_verify_skew(grid, so, tiling, 2 * r, 0)
+    assert not ok and "invalid" in why
