@@ -133,12 +133,12 @@ class ClockSampler:
 # source files of each pass kernel variant: overlapped halos (0-2), skewed
 # wavefront (4), warp-specialised (5, 6); the kernel files include wave_pass.cuh
 def kernel_sources(variant):
-    extra = {4: ("wave_skew.cuh",), 5: ("wave_lean.cuh",), 6: ("wave_lean.cuh",)}.get(variant, ())
+    extra = {4: ("wave_skew.cuh",), 5: ("wave_lean.cuh",), 6: ("wave_lean.cuh",), 7: ("wave_lean.cuh",)}.get(variant, ())
     return ("wave_pass.cuh",) + extra
 
 
 def kernel_name(so, T, variant):
-    base = {4: "skew_kernel", 5: "lean_kernel", 6: "lean_kernel"}.get(variant, "pass_kernel")
+    base = {4: "skew_kernel", 5: "lean_kernel", 6: "lean_kernel", 7: "lean_kernel"}.get(variant, "pass_kernel")
     return "%s<%d,%d> (SO%d, T=%d, variant %d)" % (base, so // 2, T, so, T, variant)
 
 

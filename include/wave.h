@@ -64,7 +64,10 @@ typedef struct wave_plan_s* wave_plan_t;
  *            tcgen05.ld; no register queue); 4 = skewed wavefront tiling in y
  *            (T = 2, tensor memory); 5 and 6 = warp-specialised pass (a
  *            producer warp issues the TMA copies, no block-wide barrier per
- *            plane, tensor memory), 1 (5) or 2 (6) rows per thread.
+ *            plane, tensor memory), 1 (5) or 2 (6) rows per thread; 7 =
+ *            the warp-specialised pass with 2 rows per thread whose x
+ *            queues are tensor-memory shift registers (half the tensor
+ *            memory of 6, so taller tiles and more warps).
  *            Every variant computes bit-identical fields.
  * (T, by, bz, unroll) must name a compiled kernel variant (wave_tiling_check).
  * Fields T, by, bz, xc of 0 = let the library choose. */
@@ -141,7 +144,7 @@ wave_status wave_set_receivers(wave_plan_t plan, int nrec, const double* xyz);
 /* Force the tiling of the forward passes (see wave_tiling).  T = 1 selects a
  * one-step pass (one time step per pass over HBM: the plain, untiled method)
  * in the variant that `unroll` names: 0, 1 or 2 = the block-barrier pass
- * (wave_pass.cuh), 5 or 6 = the warp-specialised pass (wave_lean.cuh).  All
+ * (wave_pass.cuh), 5, 6 or 7 = the warp-specialised pass (wave_lean.cuh).  All
  * one-step variants compute the same bits; the benchmark's untiled baseline is
  * the fastest of them.  Fields of 0 are chosen by the library.  Rejects a
  * schedule the tile-legality scheduler does not accept (WAVE_ERR_ARG).  A

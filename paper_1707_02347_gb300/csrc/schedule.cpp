@@ -66,8 +66,8 @@ bool make_geom(const int grid[3], int R, const wave_tiling& t, PassGeom* g, std:
     G.a_rows = G.r1y + 2 * R;
     G.a_cols = G.b_cols + 2 * ZH;
     G.threads = G.qz * G.r1y;
-    // variants 5, 6: one compute thread per 1 or 2 rows of a quad, plus the producer warp
-    G.block = (t.unroll == 5 || t.unroll == 6) ? G.threads / (t.unroll - 4) + 32 : G.threads;
+    // variants 5, 6, 7: one compute thread per 1 or 2 rows of a quad, plus the producer warp
+    G.block = (t.unroll == 5) ? G.threads + 32 : (t.unroll == 6 || t.unroll == 7) ? G.threads / 2 + 32 : G.threads;
     G.shape = find_pass_shape(R, t.T, G.qz, G.r1y, t.unroll);
     if (!G.shape && need_kernel)
         return no("no compiled kernel for SO " + std::to_string(2 * R) + ", T = " + std::to_string(t.T) +

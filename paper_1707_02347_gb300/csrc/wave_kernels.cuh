@@ -60,7 +60,8 @@ struct PassShape {
     int R, T, qz, ry;
     int unroll;  // variant: x-queue storage 0 = registers (moved), 1 = registers (loop unrolled),
                  // 2 = tensor memory; 4 = skewed wavefront tiling in y (T = 2, tensor memory);
-                 // 5, 6 = warp-specialised pass (tensor memory), 1 or 2 rows per thread
+                 // 5, 6 = warp-specialised pass (tensor memory), 1 or 2 rows per thread;
+                 // 7 = warp-specialised pass, 2 rows per thread, tensor-memory shift registers
     size_t smem;
     cudaError_t (*launch)(const CUtensorMap& mapA, const CUtensorMap& mapV, const CUtensorMap& mapK,
                           const PassArgs& a, int threads, size_t smem, long long blocks, cudaStream_t st);

@@ -18,30 +18,48 @@
 // first step of a plane while others finish the last step of the one before.
 //
 // Work per thread.  A compute thread owns NY consecutive rows of one z quad
-// (variant 5: NY = 1, variant 6: NY = 2).  The y neighbours of its rows form
-// one column of 2r + NY quads, loaded once for all NY rows, and the per-plane
-// bookkeeping of the thread is shared by its NY quads.
+// (variant 5: NY = 1, variants 6 and 7: NY = 2).  The y neighbours of its rows
+// form one column of 2r + NY quads, loaded once for all NY rows, and the
+// per-plane bookkeeping of the thread is shared by its NY quads.
+//
+// x queues (SH).  Variants 5 and 6 keep each queue as a mirrored ring in
+// tensor memory: every plane is stored twice, so that the window of 2r
+// planes is always 8r consecutive columns.  Variant 7 (SH) keeps it as a
+// shift register of 2r planes: the window is loaded, used, and stored back
+// one plane further on (the oldest plane dropped, the newest appended) with
+// one tcgen05.st of the same registers.  That halves the tensor memory of a
+// queue, which lets two rows per thread run with 12 compute warps; the
+// delay line of the previous level (steps k >= 1) moves from shared memory
+// into tensor memory too, and the copies run two iterations ahead instead of
+// three, which frees the shared memory of a taller tile.
 #pragma once
 #include "wave_pass.cuh"
 
 namespace wave {
 namespace detail {
 
-template <int R, int T, int QZ, int RY, int NY>
+template <int R, int T, int QZ, int RY, int NY, bool SH = false>
 struct LeanGeo {
     static_assert(RY % NY == 0, "whole row groups");
     static constexpr int NC = QZ * RY / NY;  // compute threads
     static_assert(NC % 32 == 0, "whole compute warps");
     static constexpr int NW = NC / 32;       // compute warps
     static constexpr int NTHR = NC + 32;     // and one producer warp
-    static constexpr int NA = Cfg<R, T>::NA, NB = Cfg<R, T>::NB;
+    // iterations copied ahead: two where the rings of a taller tile, or of
+    // three steps, or the kappa delay line of radius 4 need the room
+    static constexpr int D = (SH || (T >= 2 && (R == 4 || T >= 3))) ? 2 : Cfg<R, T>::D;
+    static constexpr int NA = D + R + 1, NB = D + 1;
     static constexpr int NPF = 2 * (T - 1);  // plane buffers of the steps k >= 1, two per step
     // mbarriers: full A [NA], full B [NB], empty A [NA], empty B [NB], planes full [NPF]
     static constexpr int NBAR = 2 * (NA + NB) + NPF;
     static constexpr uint32_t HDR = (8u * NBAR + 8u + 127u) & ~127u;
-    // tensor memory: per quad and step a mirrored ring of 2r planes (16 r columns)
-    static constexpr int CPQ = 16 * R;
-    static constexpr int CPW = T * NY * CPQ;  // columns of one warp's lanes
+    // tensor memory per quad and step: a mirrored ring of 2r planes (16 r
+    // columns) or (SH) a shift register of 2r planes (8 r columns); SH also
+    // keeps the previous-level delay line of the steps k >= 1 (r slots of 4
+    // columns per row) after the queues
+    static constexpr int CPQ = SH ? 8 * R : 16 * R;
+    static constexpr int VCOL = T * NY * CPQ;                  // first delay-line column of a warp
+    static constexpr int CPW = VCOL + (SH ? (T - 1) * NY * R * 4 : 0);  // columns of one warp's lanes
     static constexpr int WPQ = (NW + 3) / 4;  // warps sharing a lane quarter
     static constexpr int NEED = WPQ * CPW;
     static constexpr int COLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
@@ -107,14 +125,41 @@ __device__ __forceinline__ void tmem_ld_window(uint32_t taddr, uint32_t (&w)[8 *
     if constexpr (R == 8) tmem_ld_x64(taddr, w);
 }
 
-template <int R, int T, int QZ, int RY, int NY>
-__global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_blocks<R, T, QZ, RY, NY>())
+// the window of an x queue (8 r columns) stored from w, shifted by one plane:
+// columns [0, 8r - 4) take w[4 ..], the last 4 take the newest plane
+template <int R>
+__device__ __forceinline__ void tmem_st_shift(uint32_t taddr, const uint32_t (&w)[8 * R], const float4& nw)
+{
+    if constexpr (R == 2) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16};" ::"r"(taddr),
+            "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]),
+            "r"(w[13]), "r"(w[14]), "r"(w[15]), "r"(__float_as_uint(nw.x)), "r"(__float_as_uint(nw.y)),
+            "r"(__float_as_uint(nw.z)), "r"(__float_as_uint(nw.w)));
+    }
+    if constexpr (R == 4) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::
+                "r"(taddr),
+            "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]),
+            "r"(w[13]), "r"(w[14]), "r"(w[15]), "r"(w[16]), "r"(w[17]), "r"(w[18]), "r"(w[19]), "r"(w[20]),
+            "r"(w[21]), "r"(w[22]), "r"(w[23]), "r"(w[24]), "r"(w[25]), "r"(w[26]), "r"(w[27]), "r"(w[28]),
+            "r"(w[29]), "r"(w[30]), "r"(w[31]), "r"(__float_as_uint(nw.x)), "r"(__float_as_uint(nw.y)),
+            "r"(__float_as_uint(nw.z)), "r"(__float_as_uint(nw.w)));
+    }
+    static_assert(R == 2 || R == 4, "shift-register queues are compiled for radius 2 and 4");
+}
+
+template <int R, int T, int QZ, int RY, int NY, bool SH = false>
+__global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, lean_min_blocks<R, T, QZ, RY, NY>())
     lean_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
                 const __grid_constant__ CUtensorMap mapK, const PassArgs a)
 {
     using C = Cfg<R, T>;
     using G = Geo<R, T, QZ, RY>;
-    using L = LeanGeo<R, T, QZ, RY, NY>;
+    using L = LeanGeo<R, T, QZ, RY, NY, SH>;
     constexpr int NA = L::NA, NB = L::NB, NW = L::NW, NC = L::NC, ZH = C::ZH, R2 = 2 * R;
     constexpr int afl = G::AFL, bfl = G::BFL, pitch = G::A_COLS;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -124,7 +169,10 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
     float* __restrict__ ringA = reinterpret_cast<float*>(smem + L::HDR);
     float* __restrict__ ringB = ringA + NA * afl;
     float* __restrict__ planes = ringB + NB * 2 * bfl;
+    // (not SH) the delay lines of steps k >= 1: the previous level's
+    // increment and kappa of the plane, r iterations from step k-1 to step k
     float4* __restrict__ vring = reinterpret_cast<float4*>(planes + 2 * (T - 1) * afl);
+    float4* __restrict__ kring = vring + (T - 1) * R * NY * L::NC;
     const uint32_t fullA = smem_u32(smem), fullB = fullA + 8 * NA, emptyA = fullB + 8 * NB,
                    emptyB = emptyA + 8 * NA, fullP = emptyB + 8 * NB;
     constexpr uint32_t txA = static_cast<uint32_t>(G::A_ROWS * G::A_COLS * 4);
@@ -281,8 +329,12 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
         // this warp's tensor-memory columns: lane quarter (warp % 4), column block (warp / 4)
         const uint32_t twarp =
             *s_tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + static_cast<uint32_t>((warp >> 2) * L::CPW);
-        // column of slot s (0 .. 4r - 1) of the ring of step k, row r
+        // column of slot s (0 .. 4r - 1, or 0 .. 2r - 1 for SH) of the queue of step k, row r
         auto tcol = [&](int k, int r, int s) { return twarp + static_cast<uint32_t>((k * NY + r) * L::CPQ + 4 * s); };
+        // (SH) column of slot s (0 .. r - 1) of the previous-level delay line of step k >= 1, row r
+        auto vcol = [&](int k, int r, int s) {
+            return twarp + static_cast<uint32_t>(L::VCOL + (((k - 1) * NY + r) * R + s) * 4);
+        };
 
         // ring positions of iteration i, advanced incrementally
         int sA = 0, sAc = NA - R, sB = 0;  // i % NA, (i - R) % NA, i % NB
@@ -297,7 +349,8 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
         auto body = [&](int i, auto nact_c, auto out_c) {
             constexpr int NACT = decltype(nact_c)::value;
             constexpr bool OUTP = decltype(out_c)::value;
-            // kappa of steps k >= 1 at their planes, fetched early (cache hits)
+            // (SH) kappa of steps k >= 1 at their planes, fetched early (cache
+            // hits); otherwise it comes down the delay line from step k-1
             float4 kpre[T][NY];
 #pragma unroll
             for (int k = 1; k < T; ++k) {
@@ -305,7 +358,7 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
 #pragma unroll
                 for (int r = 0; r < NY; ++r) {
                     kpre[k][r] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (k < NACT && k < wsteps && colv[r] && xk >= 0 && xk < a.nx)
+                    if (SH && k < NACT && k < wsteps && colv[r] && xk >= 0 && xk < a.nx)
                         kpre[k][r] = __ldg(reinterpret_cast<const float4*>(a.kap + xk * sx + colofs[r]));
                 }
             }
@@ -319,7 +372,7 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
                 float* pl = planes + ((k - 1) * 2 + (i & 1)) * afl + posA0;
                 if (k < NACT && k <= wsteps) {
                     // (uniform over the warp, as every tcgen05 access)
-                    const int sc = ts + R < R2 ? ts + R : ts - R;
+                    const int sc = SH ? R : (ts + R < R2 ? ts + R : ts - R);
                     uint32_t c4[NY][4];
 #pragma unroll
                     for (int r = 0; r < NY; ++r) tmem_ld_x4(tcol(k, r, sc), c4[r]);
@@ -354,7 +407,7 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
             const float* pnew = ringA + sA * afl;
             const float* pctr = ringA + sAc * afl;
             const float* pb = ringB + sB * 2 * bfl;
-            float4 pu[NY], pv[NY];  // u, v of the latest step computed in this iteration
+            float4 pu[NY], pv[NY], pk[NY];  // u, v and kappa of the latest step computed in this iteration
 
             // Step k of the pass at plane x_k = x_0 - k r for the NY rows:
             // plane holds its input level with the y-z halo; newest[r] is the
@@ -374,7 +427,7 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
                 // the first window load overlaps the y sums
                 __syncwarp();
                 uint32_t w[4 * R2];
-                tmem_ld_window<R>(tcol(k, 0, ts), w);
+                tmem_ld_window<R>(tcol(k, 0, SH ? 0 : ts), w);
                 // Ly of every row, the pairs k' = 1 .. r taken in order for each
                 // row (the same operations as laplacian_y), rows interleaved so
                 // that only a sliding part of the y column is live
@@ -400,12 +453,16 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
                     // (the warp may have diverged on the previous row's events)
                     if constexpr (r > 0) {
                         __syncwarp();
-                        tmem_ld_window<R>(tcol(k, r, ts), w);
+                        tmem_ld_window<R>(tcol(k, r, SH ? 0 : ts), w);
                     }
+                    // (SH, steps k >= 1) the previous level of this row, from the delay line
+                    uint32_t pv4[4] = {0u, 0u, 0u, 0u};
+                    if constexpr (SH && k >= 1) tmem_ld_x4(vcol(k, r, vs), pv4);
                     const float4 c = cen[r];
                     float2 zl, zh, xl, xh;
                     laplacian_z<R>(plane, posA0 + r * pitch, c, a, zl, zh);
                     tmem_wait_ld(w);
+                    if constexpr (SH && k >= 1) tmem_wait_ld(pv4);
                     auto xq = [&](auto jc) -> float4 {
                         constexpr int j = decltype(jc)::value;
                         if constexpr (j == R2) {
@@ -416,6 +473,8 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
                         }
                     };
                     laplacian_x<R>(c, xq, a, xl, xh);
+                    // (SH) the queue advances: the window shifted by one plane, the newest appended
+                    if constexpr (SH) tmem_st_shift<R>(tcol(k, r, 0), w, newest[r]);
                     float4 Lq = combine(yl[r], yh[r], zl, zh, xl, xh);
                     if (xk == nxt[k][r]) {
                         // sources of this plane (before the update) ...
@@ -434,9 +493,19 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
                         scur[k][r] = e0;
                     }
                     float4 u = c;
-                    float4 v = (k == 0) ? lds4(pb + (ty0 + r) * G::B_COLS + 4 * tq)
-                                        : vring[(((k - 1) * R + vs) * NY + r) * NC + tid];
-                    const float4 kp = (k == 0) ? lds4(pb + bfl + (ty0 + r) * G::B_COLS + 4 * tq) : kpre[k][r];
+                    float4 v;
+                    if constexpr (k == 0) {
+                        v = lds4(pb + (ty0 + r) * G::B_COLS + 4 * tq);
+                    } else if constexpr (SH) {
+                        v = make_float4(__uint_as_float(pv4[0]), __uint_as_float(pv4[1]), __uint_as_float(pv4[2]),
+                                        __uint_as_float(pv4[3]));
+                    } else {
+                        v = vring[(((k - 1) * R + vs) * NY + r) * NC + tid];
+                    }
+                    float4 kp;
+                    if constexpr (k == 0) kp = lds4(pb + bfl + (ty0 + r) * G::B_COLS + 4 * tq);
+                    else if constexpr (SH) kp = kpre[k][r];
+                    else kp = kring[(((k - 1) * R + vs) * NY + r) * NC + tid];
                     if (fast) {
                         const float2 vl = __ffma2_rn(lo2(kp), lo2(Lq), lo2(v));
                         const float2 vh = __ffma2_rn(hi2(kp), hi2(Lq), hi2(v));
@@ -466,6 +535,7 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
                     }
                     pu[r] = u;
                     pv[r] = v;
+                    pk[r] = kp;
                 });
             };
 
@@ -476,12 +546,25 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
                 for (int r = 0; r < NY; ++r) nw[r] = lds4(pnew + posA0 + r * pitch);
                 if constexpr (NACT >= 1) run_step(std::integral_constant<int, 0>{}, pctr, nw);
                 // the newest plane into the ring (slot i % 2r and its mirror),
-                // after this iteration's window was read
+                // after this iteration's window was read; (SH) run_step
+                // advanced the shift register, else it is advanced here
                 __syncwarp();
+                if constexpr (SH) {
+                    if constexpr (NACT < 1) {
 #pragma unroll
-                for (int r = 0; r < NY; ++r) {
-                    tmem_st4(tcol(0, r, ts), nw[r]);
-                    tmem_st4(tcol(0, r, ts + R2), nw[r]);
+                        for (int r = 0; r < NY; ++r) {
+                            uint32_t w[4 * R2];
+                            tmem_ld_window<R>(tcol(0, r, 0), w);
+                            tmem_wait_ld(w);
+                            tmem_st_shift<R>(tcol(0, r, 0), w, nw[r]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < NY; ++r) {
+                        tmem_st4(tcol(0, r, ts), nw[r]);
+                        tmem_st4(tcol(0, r, ts + R2), nw[r]);
+                    }
                 }
             }
             // step 1 is done with ring B's slot and with ring A's centre plane
@@ -503,23 +586,43 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
                     return;
                 }
                 if (k <= NACT && k <= wsteps) {
-                    float4 nw[NY], vin[NY];
+                    float4 nw[NY], vin[NY], kin[NY];
 #pragma unroll
                     for (int r = 0; r < NY; ++r) {
                         nw[r] = pu[r];
                         vin[r] = pv[r];
+                        kin[r] = pk[r];
                     }
-                    if (k < NACT && k < wsteps)
-                        run_step(std::integral_constant<int, k>{}, planes + ((k - 1) * 2 + (i & 1)) * afl, nw);
+                    const bool comp = k < NACT && k < wsteps;
+                    if (comp) run_step(std::integral_constant<int, k>{}, planes + ((k - 1) * 2 + (i & 1)) * afl, nw);
                     // the increment of step k-1 waits r iterations for step k
                     // (its slot was read above, by the step r iterations later)
-#pragma unroll
-                    for (int r = 0; r < NY; ++r) vring[(((k - 1) * R + vs) * NY + r) * NC + tid] = vin[r];
                     __syncwarp();
+                    if constexpr (SH) {
 #pragma unroll
-                    for (int r = 0; r < NY; ++r) {
-                        tmem_st4(tcol(k, r, ts), nw[r]);
-                        tmem_st4(tcol(k, r, ts + R2), nw[r]);
+                        for (int r = 0; r < NY; ++r) tmem_st4(vcol(k, r, vs), vin[r]);
+                        if (!comp) {
+                            // the queue of a step this warp does not compute still advances
+#pragma unroll
+                            for (int r = 0; r < NY; ++r) {
+                                uint32_t w[4 * R2];
+                                tmem_ld_window<R>(tcol(k, r, 0), w);
+                                tmem_wait_ld(w);
+                                tmem_st_shift<R>(tcol(k, r, 0), w, nw[r]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < NY; ++r) {
+                            vring[(((k - 1) * R + vs) * NY + r) * NC + tid] = vin[r];
+                            kring[(((k - 1) * R + vs) * NY + r) * NC + tid] = kin[r];
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int r = 0; r < NY; ++r) {
+                            tmem_st4(tcol(k, r, ts), nw[r]);
+                            tmem_st4(tcol(k, r, ts + R2), nw[r]);
+                        }
                     }
                 }
             });
@@ -560,24 +663,24 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY>::NTHR, lean_min_bloc
     if (warp == 0) tmem_dealloc(*s_tmem, L::COLS);
 }
 
-// Shared memory of the (R, T, QZ, RY, NY) instantiation.
-template <int R, int T, int QZ, int RY, int NY>
+// Shared memory of the (R, T, QZ, RY, NY, SH) instantiation.
+template <int R, int T, int QZ, int RY, int NY, bool SH = false>
 constexpr size_t lean_smem_bytes()
 {
     using G = Geo<R, T, QZ, RY>;
-    using L = LeanGeo<R, T, QZ, RY, NY>;
+    using L = LeanGeo<R, T, QZ, RY, NY, SH>;
     return L::HDR + 4u * (static_cast<size_t>(L::NA) * G::AFL + 2u * L::NB * G::BFL + 2u * (T - 1) * G::AFL) +
-           16u * static_cast<size_t>(T - 1) * R * NY * L::NC;
+           (SH ? 0u : 2u * 16u * static_cast<size_t>(T - 1) * R * NY * L::NC);
 }
 
-template <int R, int T, int QZ, int RY, int NY>
+template <int R, int T, int QZ, int RY, int NY, bool SH = false>
 cudaError_t launch_lean(const CUtensorMap& mapA, const CUtensorMap& mapV, const CUtensorMap& mapK, const PassArgs& a,
                         int /*threads: fixed by the instantiation*/, size_t smem, long long blocks, cudaStream_t st)
 {
-    auto fn = lean_kernel<R, T, QZ, RY, NY>;
+    auto fn = lean_kernel<R, T, QZ, RY, NY, SH>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    fn<<<static_cast<unsigned>(blocks), LeanGeo<R, T, QZ, RY, NY>::NTHR, smem, st>>>(mapA, mapV, mapK, a);
+    fn<<<static_cast<unsigned>(blocks), LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, smem, st>>>(mapA, mapV, mapK, a);
     return cudaGetLastError();
 }
 

@@ -13,6 +13,9 @@ namespace wave {
 // variants 5 and 6: warp-specialised pass, NY = 1 or 2 rows per thread, x queues in tensor memory
 #define WAVE_LEAN(T, QZ, RY, NY) \
     {2, T, QZ, RY, 4 + NY, detail::lean_smem_bytes<2, T, QZ, RY, NY>(), &detail::launch_lean<2, T, QZ, RY, NY>}
+// variant 7: warp-specialised pass, 2 rows per thread, x queues as tensor-memory shift registers
+#define WAVE_LEAN7(T, QZ, RY) \
+    {2, T, QZ, RY, 7, detail::lean_smem_bytes<2, T, QZ, RY, 2, true>(), &detail::launch_lean<2, T, QZ, RY, 2, true>}
 // variant 4: skewed wavefront tiling in y, T = 2, x queues in tensor memory
 #define WAVE_SKEW(QZ, RY) {2, 2, QZ, RY, 4, detail::skew_smem_bytes<2, QZ, RY>(), &detail::launch_skew<2, QZ, RY>}
 
@@ -47,6 +50,8 @@ const PassShape* pass_shapes_r2(int* n)
         WAVE_LEAN(3, 16, 32, 1),
         WAVE_LEAN(1, 16, 8, 1),
         WAVE_LEAN(1, 16, 16, 1),
+        WAVE_LEAN7(2, 16, 44),
+        WAVE_LEAN7(3, 16, 44),
     };
     *n = static_cast<int>(sizeof(shapes) / sizeof(shapes[0]));
     return shapes;

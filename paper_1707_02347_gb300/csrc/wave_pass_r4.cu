@@ -2,7 +2,8 @@
 // Each entry is one (T, z quads per row, thread rows, queue storage) variant the
 // autotuner can pick; queue storage 0/1 = registers (moved / rotated), 2 = tensor memory;
 // variant 4 = two-step pass with skewed wavefront tiling in y (tensor-memory queues);
-// variant 5 = warp-specialised pass with 1 row per thread (tensor-memory queues).
+// variant 5 = warp-specialised pass with 1 row per thread (tensor-memory queues);
+// variant 7 = warp-specialised pass with 2 rows per thread (tensor-memory shift registers).
 #include "wave_lean.cuh"
 #include "wave_skew.cuh"
 
@@ -13,6 +14,9 @@ namespace wave {
 // variants 5 and 6: warp-specialised pass, NY = 1 or 2 rows per thread, x queues in tensor memory
 #define WAVE_LEAN(T, QZ, RY, NY) \
     {4, T, QZ, RY, 4 + NY, detail::lean_smem_bytes<4, T, QZ, RY, NY>(), &detail::launch_lean<4, T, QZ, RY, NY>}
+// variant 7: warp-specialised pass, 2 rows per thread, x queues as tensor-memory shift registers
+#define WAVE_LEAN7(T, QZ, RY) \
+    {4, T, QZ, RY, 7, detail::lean_smem_bytes<4, T, QZ, RY, 2, true>(), &detail::launch_lean<4, T, QZ, RY, 2, true>}
 // variant 4: skewed wavefront tiling in y, T = 2, x queues in tensor memory
 #define WAVE_SKEW(QZ, RY) {4, 2, QZ, RY, 4, detail::skew_smem_bytes<4, QZ, RY>(), &detail::launch_skew<4, QZ, RY>}
 
@@ -44,6 +48,7 @@ const PassShape* pass_shapes_r4(int* n)
         WAVE_LEAN(2, 16, 32, 1),
         WAVE_LEAN(1, 16, 8, 1),
         WAVE_LEAN(1, 16, 16, 1),
+        WAVE_LEAN7(2, 16, 44),
     };
     *n = static_cast<int>(sizeof(shapes) / sizeof(shapes[0]));
     return shapes;

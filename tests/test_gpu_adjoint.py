@@ -194,7 +194,8 @@ def test_fwi_autograd_function(W, oracle):
     plan.close()
 
 
-@pytest.mark.parametrize("tiling", [(2, 28, 56, 34, 4), (2, 24, 56, 34, 2), (1, 8, 64, 34, 2), (2, 24, 56, 34, 5)])
+@pytest.mark.parametrize("tiling", [(2, 28, 56, 34, 4), (2, 24, 56, 34, 2), (1, 8, 64, 34, 2), (2, 24, 56, 34, 5),
+                                    (2, 36, 56, 34, 7)])
 def test_gradient_independent_of_pass_variant(W, oracle, tiling):
     """The gradient runs its forward and adjoint sweeps with the plan's
     tiling: the skewed wavefront variant, the tensor-memory T = 2 pass, the

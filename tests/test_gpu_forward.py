@@ -94,13 +94,14 @@ def test_plain_forward_64_so4_vs_oracle(W, oracle):
     (4, (37, 34, 30), [(1, 16, 64, 11), (2, 28, 24, 9), (3, 24, 24, 40), (4, 12, 48, 13), (1, 16, 64, 37, 1),
                        (2, 12, 56, 30, 1), (3, 24, 24, 19, 1), (1, 16, 64, 37, 2), (2, 28, 56, 30, 2),
                        (3, 24, 56, 19, 2), (2, 20, 56, 20, 2), (4, 20, 16, 13, 2), (2, 30, 56, 30, 4),
-                       (2, 28, 56, 13, 5), (3, 24, 56, 19, 5), (1, 8, 64, 37, 5), (1, 16, 64, 11, 5)]),
+                       (2, 28, 56, 13, 5), (3, 24, 56, 19, 5), (1, 8, 64, 37, 5), (1, 16, 64, 11, 5),
+                       (2, 40, 56, 30, 7), (3, 36, 56, 19, 7), (3, 36, 56, 37, 7)]),
     (8, (41, 35, 38), [(1, 32, 32, 40), (2, 24, 24, 10), (2, 16, 56, 41), (3, 16, 16, 17), (1, 32, 32, 41, 1),
                        (1, 16, 64, 23, 1), (2, 16, 56, 41, 1), (2, 24, 24, 29, 1), (3, 16, 16, 40, 1),
                        (1, 8, 64, 41, 2), (1, 16, 64, 23, 2), (2, 16, 56, 41, 2), (2, 24, 56, 29, 2),
                        (2, 56, 24, 17, 2), (3, 16, 16, 40, 2), (1, 32, 64, 41, 2), (2, 28, 56, 41, 4),
                        (2, 60, 24, 13, 4), (2, 24, 56, 29, 5), (2, 24, 56, 17, 5), (1, 8, 64, 41, 5),
-                       (1, 16, 64, 23, 5)]),
+                       (1, 16, 64, 23, 5), (2, 36, 56, 41, 7), (2, 36, 56, 17, 7)]),
     (16, (36, 33, 34), [(1, 16, 64, 12), (2, 16, 16, 12), (2, 16, 16, 40), (1, 32, 32, 7), (1, 16, 64, 36, 1),
                         (2, 16, 16, 36, 1), (1, 8, 64, 36, 2), (1, 16, 64, 12, 2), (2, 16, 16, 36, 2),
                         (1, 32, 64, 36, 2), (1, 32, 64, 36, 6), (1, 64, 32, 12, 6)]),
@@ -130,8 +131,8 @@ def test_layered_so8_long_run_vs_oracle(W, oracle):
 @pytest.mark.parametrize("so,shape,tilings", [
     # SO16: the two-row warp-specialised one-step pass the SO16 bench picks, and the one-row pass
     (16, (56, 52, 48), [(1, 64, 32, 40, 6), (1, 32, 64, 56, 2)]),
-    # SO4: the three-step warp-specialised pass and the one-step pass
-    (4, (64, 60, 56), [(3, 24, 56, 40, 5), (1, 16, 64, 64, 0)]),
+    # SO4: the three-step warp-specialised passes (one row, two rows per thread) and the one-step pass
+    (4, (64, 60, 56), [(3, 24, 56, 40, 5), (1, 16, 64, 64, 0), (3, 36, 56, 40, 7)]),
 ])
 def test_layered_long_run_vs_oracle(W, oracle, so, shape, tilings):
     """400 steps (the accumulated float32 rounding of a long run) against the

@@ -51,8 +51,8 @@ def state(oracle):
     plan.close()
     out = {}
     for T, tiling in ((1, (1, 8, 64, 64, 5)), ("T1v2", (1, 8, 64, 64, 2)), (2, (2, 24, 56, 128, 2)),
-                      ("skew", (2, 28, 56, 128, 4)), ("lean", (2, 24, 56, 256, 5))):
-        nT = 2 if T in (2, "skew", "lean") else 1
+                      ("skew", (2, 28, 56, 128, 4)), ("lean", (2, 24, 56, 256, 5)), ("v7", (2, 36, 56, 256, 7))):
+        nT = 2 if T in (2, "skew", "lean", "v7") else 1
         p = W.WavePlan(w.shape, w.spacing, SO, w.dt, nT, m, sponge_width=w.sponge_width, vmax=w.vmax, tiling=tiling)
         p.set_sources(w.src_xyz, torch.from_numpy(wav[N1:N1 + nT].copy()).to(dev))
         _, uB = p.forward(u_init=uA, want_final=True)
@@ -130,6 +130,7 @@ def test_full_size_two_one_step_passes_equal_one_t2_pass(state):
     assert np.array_equal(out["T1x2"], out[2])
     assert np.array_equal(out["T1x2"], out["skew"])  # the skewed wavefront variant of the two-step pass
     assert np.array_equal(out["T1x2"], out["lean"])  # the warp-specialised two-step pass
+    assert np.array_equal(out["T1x2"], out["v7"])  # two rows per thread, shift-register queues
 
 
 def test_full_size_one_step_variants_bit_identical(state):

@@ -147,12 +147,16 @@ def test_tiling_check_skewed_variant(W, so, tiling, ok):
     (8, (1, 8, 64, 128, 5), True), (8, (1, 16, 64, 128, 5), True),
     (4, (2, 28, 56, 128, 5), True), (4, (3, 24, 56, 128, 5), True), (4, (2, 28, 56, 128, 6), False),
     (16, (1, 64, 32, 128, 6), True), (16, (1, 32, 64, 256, 6), True), (16, (1, 32, 64, 256, 5), False),
+    # variant 7: two rows per thread, shift-register queues (11 compute warps: 44 thread rows)
+    (8, (2, 36, 56, 128, 7), True), (4, (2, 40, 56, 128, 7), True), (4, (3, 36, 56, 128, 7), True),
+    (8, (2, 24, 56, 128, 7), False), (16, (1, 64, 32, 128, 7), False),
 ])
 def test_tiling_check_warp_specialised_variants(W, so, tiling, ok):
     assert W.tiling_check((512, 512, 512), so, tiling) == ok
 
 
-@pytest.mark.parametrize("so,tiling", [(8, (2, 24, 56, 16, 5)), (4, (3, 24, 56, 9, 5)), (16, (1, 64, 32, 8, 6))])
+@pytest.mark.parametrize("so,tiling", [(8, (2, 24, 56, 16, 5)), (4, (3, 24, 56, 9, 5)), (16, (1, 64, 32, 8, 6)),
+                                       (8, (2, 36, 56, 16, 7)), (4, (3, 36, 56, 9, 7))])
 def test_warp_specialised_schedule_is_legal(W, so, tiling):
     # same tiles and skew as the overlapped pass; only the synchronisation differs
     ok, msg = W.schedule_verify((40, 36, 44), so, tiling)
