@@ -1435,6 +1435,8 @@ wave_status batch_persistent_build(wave_batch_t b, bool* ok)
                 BatchDesc d;
                 d.shot = static_cast<int>(i);
                 d.shape = batch_shape_index(p->R, lv.g->T, lv.g->qz, lv.g->r1y, 2);
+                d.team = batch_shape_is_team(d.shape) ? 1 : 0;
+                d.ntiles = static_cast<int>(lv.g->blocks);
                 it = seen.emplace(key, static_cast<int>(descs.size())).first;
                 descs.push_back(d);
                 args.push_back(a);
@@ -1454,7 +1456,10 @@ wave_status batch_persistent_build(wave_batch_t b, bool* ok)
             if (L >= levels[i].size()) continue;
             any = true;
             const Level& lv = levels[i][L];
-            for (long long t = 0; t < lv.g->blocks; ++t) items.push_back(make_int4(dlev[i][L], static_cast<int>(t), cum[i], lv.n0));
+            const int d = dlev[i][L];
+            const int step = descs[d].team ? 4 : 1;  // a team item covers four tiles
+            for (long long t = 0; t < lv.g->blocks; t += step)
+                items.push_back(make_int4(d, static_cast<int>(t), cum[i], lv.n0));
             cum[i] += static_cast<int>(lv.g->blocks);
         }
         if (!any) break;

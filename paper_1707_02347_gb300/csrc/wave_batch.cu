@@ -5,7 +5,9 @@
 // pass, tile) item, and each thread block (one per SM) takes the next item
 // from an atomic counter, runs that output tile of that pass (pass_tile, the
 // same code and arithmetic as the standalone pass kernel) and then publishes
-// the tile on the shot's completion counter.  A pass of a shot may start
+// the tile on the shot's completion counter.  An item of a one-step team
+// shape covers four consecutive tiles, run side by side by the block's four
+// teams of 128 threads (the occupancy a one-step tile has on its own).  A pass of a shot may start
 // only once every tile of the shot's previous pass is done: it reads their
 // outputs, with halos, and may overwrite their inputs.  The per-problem
 // tiling is the autotuner's pick for each shot (the paper's per-problem
@@ -36,8 +38,11 @@ namespace detail {
 // written by the batch's graph before its persistent launch.
 __constant__ PassArgs c_batch_args[kMaxBatchArgs];
 
-// The compiled shapes of the persistent kernel: 512-thread blocks with the x
-// queues in tensor memory (variant 2); radius, T, z quads per row, rows.
+// The compiled shapes of the persistent kernel, all with the x queues in
+// tensor memory (variant 2): radius, T, z quads per row, rows.  Block shapes
+// use all 512 threads of a block for one tile; team shapes (one-step, 128
+// threads) run four tiles at once, one per team of four warps, each team
+// with its own named barrier, shared memory and tensor-memory columns.
 #define WAVE_BATCH_SHAPES(X) \
     X(0, 2, 1, 16, 32)       \
     X(1, 2, 2, 16, 32)       \
@@ -46,10 +51,38 @@ __constant__ PassArgs c_batch_args[kMaxBatchArgs];
     X(4, 4, 1, 16, 32)       \
     X(5, 4, 2, 16, 32)       \
     X(6, 4, 2, 8, 64)
+#define WAVE_BATCH_TEAM_SHAPES(X) \
+    X(7, 2, 1, 16, 8)             \
+    X(8, 4, 1, 16, 8)
+
+constexpr int kTeams = 4, kTeamThreads = 128;
+
+// shared memory and tensor-memory columns of one team (the largest team shape)
+constexpr size_t team_smem()
+{
+    size_t m = 0;
+#define WAVE_TEAM_SMEM(I, R, T, QZ, RY) m = smem_bytes<R, T, QZ, RY>() > m ? smem_bytes<R, T, QZ, RY>() : m;
+    WAVE_BATCH_TEAM_SHAPES(WAVE_TEAM_SMEM)
+#undef WAVE_TEAM_SMEM
+    return (m + 127) & ~static_cast<size_t>(127);
+}
+constexpr uint32_t team_cols()
+{
+    uint32_t m = 0;
+#define WAVE_TEAM_COLS(I, R, T, QZ, RY) \
+    m = TmemGeo<R, T, QZ, RY>::COLS > static_cast<int>(m) ? static_cast<uint32_t>(TmemGeo<R, T, QZ, RY>::COLS) : m;
+    WAVE_BATCH_TEAM_SHAPES(WAVE_TEAM_COLS)
+#undef WAVE_TEAM_COLS
+    return m;
+}
+constexpr size_t kTeamSmem = team_smem();
+constexpr uint32_t kTeamCols = team_cols();
+static_assert(kTeams * kTeamThreads == 512, "four teams fill a block");
+static_assert(kTeams * kTeamCols <= 512, "team tensor memory");
 
 constexpr size_t batch_smem_max()
 {
-    size_t m = 0;
+    size_t m = kTeams * kTeamSmem;
 #define WAVE_SMEM_MAX(I, R, T, QZ, RY) m = smem_bytes<R, T, QZ, RY>() > m ? smem_bytes<R, T, QZ, RY>() : m;
     WAVE_BATCH_SHAPES(WAVE_SMEM_MAX)
 #undef WAVE_SMEM_MAX
@@ -92,7 +125,7 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(const __grid_constant__ B
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_tmem;
     __shared__ int4 s_item;
-    __shared__ int s_go, s_shot, s_shape;
+    __shared__ int s_go, s_shot, s_shape, s_count;
     const int tid = threadIdx.x;
     // the block's tensor memory, for every tile it runs (512 columns cover every shape)
     if (tid < 32) {
@@ -116,6 +149,8 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(const __grid_constant__ B
                     s_item = it;
                     s_shot = shot;
                     s_shape = q.desc[it.x].shape;
+                    // tiles this item covers: one, or (team shapes) up to one per team
+                    s_count = q.desc[it.x].team ? min(kTeams, q.desc[it.x].ntiles - it.y) : 1;
                     s_go = 1;
                 } else {
                     atomicOr(q.err, 2);
@@ -129,17 +164,29 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(const __grid_constant__ B
         const CUtensorMap* m = q.maps + 3 * it.x;
         const PassArgs& a = c_batch_args[it.x];
         switch (s_shape) {
-#define WAVE_CASE(I, R, T, QZ, RY) \
-    case I: pass_tile<R, T, QZ, RY, 2>(m, m + 1, m + 2, a, it.w, it.y, smem, tbase, true); break;
+#define WAVE_CASE(I, R, T, QZ, RY)                                                          \
+    case I:                                                                                 \
+        pass_tile<R, T, QZ, RY, 2>(m, m + 1, m + 2, a, it.w, it.y, smem, tbase, true, Team{tid, 0, 512}); \
+        break;
             WAVE_BATCH_SHAPES(WAVE_CASE)
 #undef WAVE_CASE
+#define WAVE_TEAM_CASE(I, R, T, QZ, RY)                                                                      \
+    case I: {                                                                                                \
+        const int g = tid / kTeamThreads;                                                                    \
+        if (g < s_count)                                                                                     \
+            pass_tile<R, T, QZ, RY, 2>(m, m + 1, m + 2, a, it.w, it.y + g, smem + g * kTeamSmem,              \
+                                       tbase + g * kTeamCols, true, Team{tid % kTeamThreads, 1 + g, kTeamThreads}); \
+        break;                                                                                               \
+    }
+            WAVE_BATCH_TEAM_SHAPES(WAVE_TEAM_CASE)
+#undef WAVE_TEAM_CASE
             default: break;
         }
-        // publish the tile: its stores before the release of the shot's counter
+        // publish the tiles: their stores before the release of the shot's counter
         fence_proxy_async_global();
         __threadfence();
         __syncthreads();
-        if (tid == 0) red_release_add(q.done + s_shot, 1);
+        if (tid == 0) red_release_add(q.done + s_shot, s_count);
     }
     tmem_fence_before();
     __syncthreads();
@@ -155,8 +202,18 @@ int batch_shape_index(int R, int T, int qz, int ry, int unroll)
 #define WAVE_FIND(I, R_, T_, QZ, RY) \
     if (R == R_ && T == T_ && qz == QZ && ry == RY) return I;
     WAVE_BATCH_SHAPES(WAVE_FIND)
+    WAVE_BATCH_TEAM_SHAPES(WAVE_FIND)
 #undef WAVE_FIND
     return -1;
+}
+
+bool batch_shape_is_team(int shape)
+{
+#define WAVE_IS_TEAM(I, R, T, QZ, RY) \
+    if (shape == I) return true;
+    WAVE_BATCH_TEAM_SHAPES(WAVE_IS_TEAM)
+#undef WAVE_IS_TEAM
+    return false;
 }
 
 size_t batch_smem_bytes() { return detail::batch_smem_max(); }

@@ -79,11 +79,14 @@ const PassShape* find_pass_shape(int R, int T, int qz, int ry, int unroll);
 // constant array (batch_copy_args), its three tensor maps (u^n with the
 // stencil halo, v^{n-1/2}, kappa) maps[3 d .. 3 d + 2].  Items are int4
 // {descriptor, tile, tiles of the shot that must be done first, n0}, in
-// queue order.
+// queue order; an item of a team shape covers tiles [tile, tile + 4) of its
+// pass (those below ntiles).
 constexpr int kMaxBatchArgs = 112;
 struct BatchDesc {
     int shot;
     int shape;
+    int team;    // 1: a one-step team shape (four tiles per item)
+    int ntiles;  // tiles of the pass
 };
 struct BatchQueue {
     const BatchDesc* desc;
@@ -99,6 +102,7 @@ struct BatchQueue {
 // Index of the compiled batch shape (radius, T, z quads per row, rows,
 // variant) or -1; the dynamic shared memory of the kernel; its launch.
 int batch_shape_index(int R, int T, int qz, int ry, int unroll);
+bool batch_shape_is_team(int shape);
 size_t batch_smem_bytes();
 // Copy n <= kMaxBatchArgs pass arguments (device memory) into the constant
 // array the persistent kernel reads; stream-ordered (capturable).

@@ -499,6 +499,21 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar)
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// The threads that run one tile: the whole block (bar = 0), or one of
+// several teams of a block, each with a named barrier of its own.  tid is the
+// thread's index within the team.
+struct Team {
+    int tid;
+    int bar;
+    int nthreads;
+};
+
+__device__ __forceinline__ void team_sync(const Team& t)
+{
+    if (t.bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(t.bar), "r"(t.nthreads) : "memory");
+}
+
 // One output tile (thread block `blk` of the pass's grid) of a pass: the
 // body of pass_kernel, and the work item of the persistent batched kernel.
 // mapA, mapV, mapK: tensor maps (kernel parameters or global memory); a:
@@ -510,7 +525,7 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar)
 template <int R, int T, int QZ, int RY, int QM>
 __device__ __forceinline__ void pass_tile(const CUtensorMap* mapA, const CUtensorMap* mapV, const CUtensorMap* mapK,
                                           const PassArgs& a, int n0, long long blk, unsigned char* smem,
-                                          uint32_t tmem_base, bool reuse)
+                                          uint32_t tmem_base, bool reuse, const Team& team)
 {
     using C = Cfg<R, T>;
     using G = Geo<R, T, QZ, RY>;
@@ -545,7 +560,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap* mapA, const CUtenso
     // thread -> column quad.  Columns and planes outside the grid need no
     // special case: kappa is zero there (TMA zero fill, zero z padding), so
     // the update keeps u = v = 0 on them -- the zero ghost layer.
-    const int tid = threadIdx.x;
+    const int tid = team.tid;
     const int ty = tid / QZ, tq = tid % QZ;
     const int gy = ylo + ty, gz = zlo + 4 * tq;
     const bool colv = gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nzp;
@@ -607,7 +622,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap* mapA, const CUtenso
         *s_abort = 0;
         fence_mbar_init();
     }
-    __syncthreads();
+    team_sync(team);
     // this warp's columns: lane quarter (warp % 4), column block (warp / 4)
     uint32_t twarp = 0;
     if constexpr (TQ) {
@@ -702,7 +717,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap* mapA, const CUtenso
                 sts4(planes + ((k - 1) * 2 + (i & 1)) * afl + posA, ctr[k]);
             }
         }
-        __syncthreads();
+        team_sync(team);
         if (*s_abort) {
             if (tid == 0)
                 for (int j = i; j < issued; ++j) {
@@ -860,7 +875,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap* mapA, const CUtenso
         tmem_wait_st();
         tmem_fence_before();
     }
-    if (TQ || reuse) __syncthreads();
+    if (TQ || reuse) team_sync(team);
     if constexpr (TQ) tmem_fence_after();
     if (reuse && tid == 0)
         for (int s = 0; s < NA + NB; ++s) mbar_inval(smem_u32(&bars[s]));
@@ -888,7 +903,8 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
         tmem_fence_after();
         tbase = *s_tmem;
     }
-    pass_tile<R, T, QZ, RY, QM>(&mapA, &mapV, &mapK, a, a.n0, blockIdx.x, smem, tbase, false);
+    pass_tile<R, T, QZ, RY, QM>(&mapA, &mapV, &mapK, a, a.n0, blockIdx.x, smem, tbase, false,
+                                Team{static_cast<int>(threadIdx.x), 0, static_cast<int>(blockDim.x)});
     if constexpr (TQ) {
         if (threadIdx.x < 32) tmem_dealloc(tbase, TG::COLS);
     }

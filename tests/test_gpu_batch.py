@@ -179,10 +179,12 @@ def test_full_size_batched_shots(oracle):
         p.close()
 
 
-# tilings of the persistent batched kernel (512-thread tiles, tensor-memory
-# queues): SO4 and SO8, T = 1, 2, 3, both tile orientations
-_PERSISTENT = {4: [(1, 32, 64, 32, 2), (2, 28, 56, 32, 2), (2, 60, 24, 32, 2), (3, 24, 56, 32, 2)],
-               8: [(1, 32, 64, 32, 2), (2, 24, 56, 32, 2), (2, 56, 24, 32, 2)]}
+# tilings of the persistent batched kernel (tensor-memory queues): 512-thread
+# tiles for SO4 and SO8, T = 1, 2, 3, both tile orientations, and the
+# one-step 128-thread tile that four teams of a block run side by side
+_PERSISTENT = {4: [(1, 32, 64, 32, 2), (2, 28, 56, 32, 2), (1, 8, 64, 32, 2), (2, 60, 24, 32, 2),
+                   (3, 24, 56, 32, 2)],
+               8: [(1, 8, 64, 32, 2), (2, 24, 56, 32, 2), (1, 32, 64, 32, 2), (2, 56, 24, 32, 2)]}
 
 
 def test_persistent_batch_matches_single_plans_and_recovers_from_timeout(oracle):
@@ -199,7 +201,7 @@ def test_persistent_batch_matches_single_plans_and_recovers_from_timeout(oracle)
 
     W.load()
     dev = torch.device("cuda")
-    shots = _shots(7, 17)
+    shots = _shots(9, 17)
     plans = []
     for i, w in enumerate(shots):
         m = torch.from_numpy(np.ascontiguousarray(w.m)).to(dev)
