@@ -38,6 +38,21 @@
 namespace wave {
 namespace detail {
 
+// Shared memory of a warp-specialised pass that copies D iterations ahead:
+// the mbarrier header, the ring of NA = D + r + 1 halo boxes of u^n, the
+// ring of NB = D + 1 (v, kappa) planes, the planes of steps k >= 1 and, unless
+// SH, their delay lines (previous increment and kappa).
+template <int R, int T, int QZ, int RY, int NY, bool SH>
+constexpr size_t lean_smem_for(int D)
+{
+    using G = Geo<R, T, QZ, RY>;
+    const size_t NA = D + R + 1, NB = D + 1, NC = QZ * RY / NY;
+    const size_t nbar = 2 * (NA + NB) + 2 * (T - 1);
+    const size_t hdr = (8 * nbar + 8 + 127) & ~static_cast<size_t>(127);
+    return hdr + 4 * (NA * G::AFL + 2 * NB * G::BFL + 2 * (T - 1) * G::AFL) +
+           (SH ? 0 : 2 * 16 * static_cast<size_t>(T - 1) * R * NY * NC);
+}
+
 template <int R, int T, int QZ, int RY, int NY, bool SH = false>
 struct LeanGeo {
     static_assert(RY % NY == 0, "whole row groups");
@@ -45,9 +60,10 @@ struct LeanGeo {
     static_assert(NC % 32 == 0, "whole compute warps");
     static constexpr int NW = NC / 32;       // compute warps
     static constexpr int NTHR = NC + 32;     // and one producer warp
-    // iterations copied ahead: two where the rings of a taller tile, or of
-    // three steps, or the kappa delay line of radius 4 need the room
-    static constexpr int D = (SH || (T >= 2 && (R == 4 || T >= 3))) ? 2 : Cfg<R, T>::D;
+    // iterations copied ahead: the radius's default (three, or two at radius
+    // 8) where the shared memory holds it, else two; two for SH
+    static constexpr int D = (SH || lean_smem_for<R, T, QZ, RY, NY, SH>(Cfg<R, T>::D) > 227u * 1024u)
+                                 ? 2 : Cfg<R, T>::D;
     static constexpr int NA = D + R + 1, NB = D + 1;
     static constexpr int NPF = 2 * (T - 1);  // plane buffers of the steps k >= 1, two per step
     // mbarriers: full A [NA], full B [NB], empty A [NA], empty B [NB], planes full [NPF]
@@ -667,10 +683,7 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, lean_min_
 template <int R, int T, int QZ, int RY, int NY, bool SH = false>
 constexpr size_t lean_smem_bytes()
 {
-    using G = Geo<R, T, QZ, RY>;
-    using L = LeanGeo<R, T, QZ, RY, NY, SH>;
-    return L::HDR + 4u * (static_cast<size_t>(L::NA) * G::AFL + 2u * L::NB * G::BFL + 2u * (T - 1) * G::AFL) +
-           (SH ? 0u : 2u * 16u * static_cast<size_t>(T - 1) * R * NY * L::NC);
+    return lean_smem_for<R, T, QZ, RY, NY, SH>(LeanGeo<R, T, QZ, RY, NY, SH>::D);
 }
 
 template <int R, int T, int QZ, int RY, int NY, bool SH = false>

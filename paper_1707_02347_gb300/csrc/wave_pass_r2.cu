@@ -47,6 +47,8 @@ const PassShape* pass_shapes_r2(int* n)
         WAVE_SHAPE(4, 8, 32, 2),
         WAVE_SKEW(16, 32),
         WAVE_LEAN(2, 16, 32, 1),
+        WAVE_LEAN(2, 16, 40, 1),
+        WAVE_LEAN(2, 16, 44, 1),
         WAVE_LEAN(3, 16, 32, 1),
         WAVE_LEAN(1, 16, 8, 1),
         WAVE_LEAN(1, 16, 16, 1),

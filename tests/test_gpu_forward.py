@@ -95,7 +95,8 @@ def test_plain_forward_64_so4_vs_oracle(W, oracle):
                        (2, 12, 56, 30, 1), (3, 24, 24, 19, 1), (1, 16, 64, 37, 2), (2, 28, 56, 30, 2),
                        (3, 24, 56, 19, 2), (2, 20, 56, 20, 2), (4, 20, 16, 13, 2), (2, 30, 56, 30, 4),
                        (2, 28, 56, 13, 5), (3, 24, 56, 19, 5), (1, 8, 64, 37, 5), (1, 16, 64, 11, 5),
-                       (2, 40, 56, 30, 7), (3, 36, 56, 19, 7), (3, 36, 56, 37, 7)]),
+                       (2, 40, 56, 30, 7), (3, 36, 56, 19, 7), (3, 36, 56, 37, 7), (2, 36, 56, 30, 5),
+                       (2, 40, 56, 13, 5)]),
     (8, (41, 35, 38), [(1, 32, 32, 40), (2, 24, 24, 10), (2, 16, 56, 41), (3, 16, 16, 17), (1, 32, 32, 41, 1),
                        (1, 16, 64, 23, 1), (2, 16, 56, 41, 1), (2, 24, 24, 29, 1), (3, 16, 16, 40, 1),
                        (1, 8, 64, 41, 2), (1, 16, 64, 23, 2), (2, 16, 56, 41, 2), (2, 24, 56, 29, 2),
