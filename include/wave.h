@@ -228,7 +228,12 @@ wave_status wave_adjoint(wave_plan_t plan, const float* rec_resid, float* src_ou
  * grad_m: device [nx][ny][nz]; misfit: host double (may be NULL).
  * checkpoint_every = K > 0 stores (u^{n-1}, u^n) every K steps and recomputes
  * each K-step segment forward before its adjoint sweep (memory ~ (nt/K + K)
- * fields); K = 0 stores every level when it fits in device memory. */
+ * fields; ~ (nt/K + 2K) when the device has room for a second segment
+ * buffer, and then the recompute of one segment runs on a second stream of
+ * the plan while the adjoint steps through the next).  K = 0 (or K >= nt)
+ * keeps every increment of one forward sweep when it fits in device memory,
+ * with no recomputation.  The imaging condition is fused into the adjoint
+ * passes.  The result does not depend on K. */
 wave_status wave_gradient(wave_plan_t plan, const float* d_obs, float* grad_m, double* misfit,
                           int checkpoint_every);
 
@@ -288,9 +293,10 @@ wave_status wave_batch_create(wave_batch_t* out, int nplans, const wave_plan_t* 
 
 /* Autotune every plan of the batch (wave_autotune with `passes` timed passes
  * per candidate) over the tilings the persistent batched kernel runs (SO 4
- * and 8: 512-thread tiles with tensor-memory queues, T = 1, 2 or 3, on x
- * slabs of 256 planes or the whole grid); plans of SO 16 are tuned over every
- * candidate. */
+ * and 8: 512-thread tiles with tensor-memory queues, T = 1, 2 or 3; x slabs
+ * of one length for the whole batch, or the whole grid: 256 planes while a
+ * pass level of all the shots makes at least two work items per SM, else
+ * 128, 64 or 32); plans of SO 16 are tuned over every candidate. */
 wave_status wave_batch_autotune(wave_batch_t batch, int passes);
 
 /* Forward modelling of every shot from zero fields, the same results as

@@ -111,11 +111,12 @@ wave_tiling default_tiling(const int grid[3], int R, int T)
 
 std::vector<wave_tiling> tiling_candidates(const int grid[3], int R)
 {
-    // every compiled shape of radius R, with three slab lengths
+    // every compiled shape of radius R, with four slab lengths (short slabs
+    // give small grids more thread blocks than the SMs hold at once)
     std::vector<wave_tiling> out;
     int n = 0;
     const PassShape* s = pass_shapes(&n);
-    const int slabs[] = {64, 128, 256};
+    const int slabs[] = {32, 64, 128, 256};
     for (int i = 0; i < n; ++i) {
         if (s[i].R != R) continue;
         int by, bz;

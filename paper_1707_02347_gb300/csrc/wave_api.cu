@@ -149,6 +149,8 @@ struct wave_plan_s {
     float* stage_r = nullptr;
     // gradient workspace
     std::vector<float*> levels;
+    cudaStream_t st2 = nullptr;                                      // recompute stream of the pipelined adjoint sweep
+    cudaEvent_t gev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // its fork and hand-off events
     size_t level_count = 0;
     float* work = nullptr;  // misc device scratch
     size_t work_bytes = 0;
@@ -284,12 +286,26 @@ wave_status ensure_skew_buffers(wave_plan_t p, const PassGeom& g)
     return WAVE_OK;
 }
 
+// Imaging condition of the gradient, fused into a one-step adjoint pass
+// (PassArgs::gacc): gacc += -(scale mu) (vn - vo) at every point.
+struct Imaging {
+    float* gacc;
+    const float* vn;
+    const float* vo;
+    float scale;
+};
+
 // gather: slots is the trace array [nt][nrec] and the traces of this
 // one-step pass are gathered from out_u after it (dense receiver surfaces);
 // otherwise slots holds tap values [nt][ntaps], reduced after the run.
+// img: imaging condition to fuse (one-step passes only).  aux: launch on the
+// plan's recompute stream st2 instead of st.
 wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const float* wavelet, float* slots, int n0,
-                     const float* u, const float* v, float* out_u, float* out_v, bool gather = false)
+                     const float* u, const float* v, float* out_u, float* out_v, bool gather = false,
+                     const Imaging* img = nullptr, bool aux = false)
 {
+    cudaStream_t st = aux ? p->st2 : p->st;
+    if (img && g.T != 1) return fail(WAVE_ERR_ARG, "the imaging condition is fused into one-step passes only");
     const CUtensorMap* mA = get_map(p, u, g.a_rows, g.a_cols);
     const CUtensorMap* mV = get_map(p, v, g.b_rows, g.b_cols);
     const CUtensorMap* mK = get_map(p, p->kap, g.b_rows, g.b_cols);
@@ -298,6 +314,12 @@ wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const
     a.n0 = n0;
     a.out_u = out_u;
     a.out_v = out_v;
+    if (img) {
+        a.gacc = img->gacc;
+        a.img_vn = img->vn;
+        a.img_vo = img->vo;
+        a.img_scale = img->scale;
+    }
     gather = gather && taps.gidx && slots && taps.nrec > 0 && g.T == 1;
     if (gather) a.rec_ptr = nullptr;
     cudaError_t e = cudaSuccess;
@@ -309,30 +331,30 @@ wave_status run_pass(wave_plan_t p, const PassGeom& g, const TapSet& taps, const
                 p->ev.push_back(x);
             }
         }
-        CK(cudaEventRecord(p->ev[p->ev_used], p->st));
+        CK(cudaEventRecord(p->ev[p->ev_used], st));
     }
     if (!g.shape) return fail(WAVE_ERR_ARG, "no compiled kernel for this tile shape");
     long long blocks = g.blocks;
     if (g.shape->unroll == 4) {
         // skewed wavefront: persistent blocks (one per SM) take the tiles in order
-        wave_status st = ensure_skew_buffers(p, g);
-        if (st) return st;
+        wave_status sb = ensure_skew_buffers(p, g);
+        if (sb) return sb;
         a.exch = p->exch;
         a.sync = p->sync;
         a.nitems = static_cast<int>(g.blocks);
         a.exch_nit = g.xc + 4 * p->R;
-        CK(cudaMemsetAsync(p->sync, 0, (g.blocks + 1) * sizeof(int), p->st));
+        CK(cudaMemsetAsync(p->sync, 0, (g.blocks + 1) * sizeof(int), st));
         blocks = std::min<long long>(g.blocks, p->sm_count);
     }
-    e = g.shape->launch(*mA, *mV, *mK, a, g.block, g.smem, blocks, p->st);
+    e = g.shape->launch(*mA, *mV, *mK, a, g.block, g.smem, blocks, st);
     p->launches++;
     if (gather && e == cudaSuccess) {
         e = launch_rec_gather(out_u, taps.gidx, taps.rec_tptr, taps.rec_tw, slots + static_cast<long long>(n0) * taps.nrec,
-                              taps.nrec, p->st);
+                              taps.nrec, st);
         p->launches++;
     }
     if (p->prof) {
-        CK(cudaEventRecord(p->ev[p->ev_used + 1], p->st));
+        CK(cudaEventRecord(p->ev[p->ev_used + 1], st));
         p->ev_used += 2;
         p->prof_points += static_cast<double>(p->n[0]) * p->n[1] * p->n[2] * g.T;
     }
@@ -346,14 +368,15 @@ struct Fields {
 
 // One pass of g.T steps on the state f.
 wave_status step_pass(wave_plan_t p, const PassGeom& g, Fields* f, const TapSet& taps, const float* wavelet,
-                      float* slots, int n0, bool gather = false)
+                      float* slots, int n0, bool gather = false, const Imaging* img = nullptr)
 {
     if (g.T == 1) {
-        wave_status s = run_pass(p, g, taps, wavelet, slots, n0, f->u, f->v, f->f0, f->v, gather);
+        wave_status s = run_pass(p, g, taps, wavelet, slots, n0, f->u, f->v, f->f0, f->v, gather, img);
         if (s) return s;
         std::swap(f->u, f->f0);  // u <- new, f0 <- old u; v updated in place
         return WAVE_OK;
     }
+    if (img) return fail(WAVE_ERR_ARG, "the imaging condition is fused into one-step passes only");
     wave_status s = run_pass(p, g, taps, wavelet, slots, n0, f->u, f->v, f->f0, f->f1);
     if (s) return s;
     std::swap(f->u, f->f0);
@@ -545,6 +568,12 @@ void destroy(wave_plan_t p)
     cudaFree(p->exch);
     cudaFree(p->sync);
     for (auto e : p->ev) cudaEventDestroy(e);
+    if (p->st2) {
+        cudaStreamSynchronize(p->st2);
+        cudaStreamDestroy(p->st2);
+    }
+    for (auto e : p->gev)
+        if (e) cudaEventDestroy(e);
     delete p;
 }
 
@@ -781,7 +810,9 @@ namespace {
 
 // wave_autotune over the candidates; batch_only keeps the shapes the
 // persistent batched kernel runs (and their one-step sweep tiling).
-wave_status autotune_impl(wave_plan_t p, int passes, int T_only, bool batch_only, wave_tiling* cand,
+// batch_xc > 0: only the persistent batched kernel's shapes, on slabs of
+// batch_xc planes (or all of x).
+wave_status autotune_impl(wave_plan_t p, int passes, int T_only, int batch_xc, wave_tiling* cand,
                           double* ms_per_step, int cap, int* ncand)
 {
     if (!p || passes < 1) return fail(WAVE_ERR_ARG, "wave_autotune: bad argument");
@@ -801,10 +832,8 @@ wave_status autotune_impl(wave_plan_t p, int passes, int T_only, bool batch_only
         if (T_only > 0 && t.T != T_only) continue;
         PassGeom geom;
         if (!make_geom(p->n, p->R, t, &geom, nullptr)) continue;
-        // batch tilings: the persistent kernel's shapes, on slabs of 256 planes (or all of x), so that
-        // the pipeline fill of a work item (2 r T planes) costs little beside its slab
-        if (batch_only && (batch_shape_index(p->R, geom.T, geom.qz, geom.r1y, t.unroll) < 0 ||
-                           t.xc != std::min(256, p->n[0])))
+        if (batch_xc > 0 && (batch_shape_index(p->R, geom.T, geom.qz, geom.r1y, t.unroll) < 0 ||
+                             t.xc != std::min(batch_xc, p->n[0])))
             continue;
         Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
         auto one = [&](int n0) -> wave_status { return step_pass(p, geom, &f, none, nullptr, nullptr, n0); };
@@ -855,7 +884,7 @@ wave_status autotune_impl(wave_plan_t p, int passes, int T_only, bool batch_only
 extern "C" wave_status wave_autotune(wave_plan_t p, int passes, int T_only, wave_tiling* cand, double* ms_per_step,
                                      int cap, int* ncand)
 {
-    return autotune_impl(p, passes, T_only, false, cand, ms_per_step, cap, ncand);
+    return autotune_impl(p, passes, T_only, 0, cand, ms_per_step, cap, ncand);
 }
 
 namespace {
@@ -1044,6 +1073,7 @@ namespace {
 // gradient_enqueue only issues stream work (and can be captured in a graph).
 struct GradPlan {
     int K = 0, nseg = 0;
+    bool pipe = false;  // two segment buffers: the recompute of segment c-1 overlaps the adjoint of segment c
 };
 
 size_t grad_rbytes(wave_plan_t p) { return static_cast<size_t>(p->nt) * p->fwd.nrec * 4; }
@@ -1073,11 +1103,36 @@ wave_status gradient_prepare(wave_plan_t p, int checkpoint_every, GradPlan* gp)
         K = need + (size_t(4) << 30) < fr ? std::max(nt, 1) : std::max(1, static_cast<int>(std::sqrt(double(nt))));
     }
     const int nseg = nt > 0 ? (nt + K - 1) / K : 0;
-    const size_t nlev = static_cast<size_t>(2 * nseg) + (K + 1) + 1;
+    // levels: the checkpoints (u, v) of every segment, then one or two
+    // segment buffers, each the K + 1 increments of a segment and a spare u.
+    // Two when there are two segments or more and the device holds them with
+    // 1 GiB to spare (or they are already allocated), unless the environment
+    // variable WAVE_GRADIENT_SERIAL is set to 1 (the serial schedule, which
+    // gives the same bits).
+    const size_t nlev1 = static_cast<size_t>(2 * nseg) + (K + 2);
+    const size_t nlev2 = nlev1 + (K + 2);
+    const char* serial = std::getenv("WAVE_GRADIENT_SERIAL");
+    bool pipe = false;
+    if (nseg >= 2 && !(serial && std::strcmp(serial, "1") == 0)) {
+        pipe = p->levels.size() >= nlev2;
+        if (!pipe) {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+                const size_t more = (nlev2 - std::min(nlev2, p->levels.size())) * static_cast<size_t>(p->npad) * 4;
+                pipe = more + (size_t(1) << 30) < fr;
+            }
+        }
+    }
+    const size_t nlev = pipe ? nlev2 : nlev1;
     while (p->levels.size() < nlev) {
         float* l = nullptr;
         CK(cudaMalloc(&l, p->npad * 4));
         p->levels.push_back(l);
+        p->gen++;
+    }
+    if (pipe && !p->st2) {
+        CK(cudaStreamCreateWithFlags(&p->st2, cudaStreamNonBlocking));
+        for (auto& e : p->gev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         p->gen++;
     }
     s = ensure_work(p, 2 * grad_rbytes(p) + 256 * 8 + 1024);
@@ -1086,6 +1141,7 @@ wave_status gradient_prepare(wave_plan_t p, int checkpoint_every, GradPlan* gp)
     if (s) return s;
     gp->K = K;
     gp->nseg = nseg;
+    gp->pipe = pipe;
     return WAVE_OK;
 }
 
@@ -1093,28 +1149,53 @@ wave_status gradient_prepare(wave_plan_t p, int checkpoint_every, GradPlan* gp)
 // start of every segment, residual and misfit partial sums, then the adjoint
 // sweep segment by segment (recompute the increments of the segment from its
 // checkpoint, then step the adjoint back through it, imaging as it goes).
+// The last segment is not recomputed: the forward keeps its increments.
+// With two segment buffers (gp.pipe) the recompute of segment c-1 runs on
+// p->st2 into one buffer while the adjoint steps through segment c on p->st
+// from the other; events order each recompute after the adjoint sweep that
+// last read its buffer, and each adjoint sweep after its recompute.  The
+// arithmetic and its order are the same on every schedule.
 wave_status gradient_enqueue(wave_plan_t p, const GradPlan& gp, const float* d_obs, float* grad_m)
 {
     const int nt = p->nt, K = gp.K, nseg = gp.nseg;
     const int nrec = p->fwd.nrec;
-    float** ck = p->levels.data();                  // [2 nseg]: (u^{cK}, v^{cK-1/2})
-    float** seg = p->levels.data() + 2 * nseg;      // [K + 1]: v^{t0-1/2} .. v^{t0+K-1/2}
-    float* uspare = p->levels[2 * nseg + K + 1];    // second u buffer of the recompute
+    const bool pipe = gp.pipe;
+    float** ck = p->levels.data();  // [2 nseg]: (u^{cK}, v^{cK-1/2})
+    // segment buffer b: [K + 1] increments v^{t0-1/2} .. v^{t0+K-1/2}, then the spare u of the recompute
+    auto segbuf = [&](int b) { return p->levels.data() + 2 * nseg + static_cast<size_t>(b) * (K + 2); };
+    auto bufof = [&](int c) { return pipe ? (c & 1) : 0; };  // segment buffer of segment c
     float* rec = p->work;
     float* rrev = grad_rrev(p);
     double* partial = grad_partial(p);
     wave_status s = WAVE_OK;
+    // one-step passes of segment c from its checkpoint, keeping every increment in buffer b
+    // (the checkpoint's u buffer is reused: each segment is visited once)
+    auto sweep = [&](int c, int b, float* slots, bool gather, bool aux) -> wave_status {
+        const int t0 = c * K;
+        const int steps = std::min(K, nt - t0);
+        float** seg = segbuf(b);
+        float* uu[2] = {ck[2 * c], seg[K + 1]};
+        CK(cudaMemcpyAsync(seg[0], ck[2 * c + 1], p->npad * 4, cudaMemcpyDeviceToDevice, aux ? p->st2 : p->st));
+        for (int l = 0; l < steps; ++l) {
+            wave_status r = run_pass(p, p->geom1, p->fwd, p->wavelet, slots, t0 + l, uu[l & 1], seg[l],
+                                     uu[(l + 1) & 1], seg[l + 1], gather, nullptr, aux);
+            if (r) return r;
+        }
+        return WAVE_OK;
+    };
     CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
-    // 1) forward, keeping a checkpoint at the start of every segment
+    // 1) forward, keeping a checkpoint at the start of every segment; the
+    // last segment in one-step passes (the same bits as the plan's tiling)
     Fields f{p->buf[0], p->buf[1], p->buf[2], p->buf[3]};
     CK(cudaMemsetAsync(f.u, 0, p->npad * 4, p->st));
     CK(cudaMemsetAsync(f.v, 0, p->npad * 4, p->st));
-    const bool gather = p->fwd.gidx != nullptr && p->geom.T == 1;  // traces gathered into rec after every pass
+    const bool gather = p->fwd.gidx != nullptr && (p->geom.T == 1 || nseg == 1);  // traces gathered after every pass
+    float* slots = gather ? rec : p->slots;
     for (int c = 0; c < nseg; ++c) {
         CK(cudaMemcpyAsync(ck[2 * c], f.u, p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
         CK(cudaMemcpyAsync(ck[2 * c + 1], f.v, p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
-        const int steps = std::min(K, nt - c * K);
-        s = advance(p, &f, p->fwd, p->wavelet, gather ? rec : p->slots, c * K, steps, true, gather);
+        s = c + 1 < nseg ? advance(p, &f, p->fwd, p->wavelet, slots, c * K, K, true, gather)
+                         : sweep(c, bufof(c), slots, gather, false);
         if (s) return s;
     }
     if (!gather) {
@@ -1132,27 +1213,46 @@ wave_status gradient_enqueue(wave_plan_t p, const GradPlan& gp, const float* d_o
     float* gacc = p->buf[0];  // gradient accumulator (padded layout)
     CK(cudaMemsetAsync(gacc, 0, p->npad * 4, p->st));
     const float scale = static_cast<float>(1.0 / (p->dt * p->dt));
-    for (int c = nseg - 1; c >= 0; --c) {
+    // adjoint steps j = t0+steps .. t0+1 of segment c: mu^j from the adjoint
+    // state, source r^{j-1}, and the imaging condition
+    // D_tt u^{j-1} = (v^{j-1/2} - v^{j-3/2}) / dt^2 fused into the pass
+    auto adjoint = [&](int c) -> wave_status {
         const int t0 = c * K;
         const int steps = std::min(K, nt - t0);
-        // recompute the increments v^{t0+1/2} .. v^{t0+steps-1/2} into seg[1 ..]
-        float* uu[2] = {ck[2 * c], uspare};
-        CK(cudaMemcpyAsync(seg[0], ck[2 * c + 1], p->npad * 4, cudaMemcpyDeviceToDevice, p->st));
-        for (int l = 0; l < steps; ++l) {
-            s = run_pass(p, p->geom1, p->fwd, p->wavelet, nullptr, t0 + l, uu[l & 1], seg[l], uu[(l + 1) & 1],
-                         seg[l + 1]);
-            if (s) return s;
-        }
-        // (the checkpoint's u buffer is reused by the recompute: each segment is visited once)
-        // adjoint steps j = t0+steps .. t0+1: mu^j from the adjoint state, source r^{j-1}
+        float** seg = segbuf(bufof(c));
         for (int j = t0 + steps; j >= t0 + 1; --j) {
-            const int sidx = nt - j;  // forward-order index of this adjoint step
-            s = step_pass(p, p->geom1, &a, p->adj, rrev, nullptr, sidx);
-            if (s) return s;
-            // D_tt u^{j-1} = (v^{j-1/2} - v^{j-3/2}) / dt^2 ; seg[l] = v^{t0+l-1/2}
             const int l = j - t0;
-            CKL(launch_grad_accum(gacc, a.u, seg[l], seg[l - 1], p->npad, scale, p->st));
+            const Imaging img{gacc, seg[l], seg[l - 1], scale};
+            wave_status r = step_pass(p, p->geom1, &a, p->adj, rrev, nullptr, nt - j, false, &img);
+            if (r) return r;
         }
+        return WAVE_OK;
+    };
+    if (!pipe) {
+        for (int c = nseg - 1; c >= 0; --c) {
+            if (c + 1 < nseg) s = sweep(c, 0, nullptr, false, false);
+            if (!s) s = adjoint(c);
+            if (s) return s;
+        }
+    } else {
+        // gev: [0] fork, [1 + b] recompute into buffer b done, [3 + b] adjoint sweep of buffer b done
+        CK(cudaEventRecord(p->gev[0], p->st));
+        CK(cudaStreamWaitEvent(p->st2, p->gev[0], 0));
+        for (int c = nseg - 1; c >= 0; --c) {
+            const int b = c & 1;
+            if (c + 1 < nseg) CK(cudaStreamWaitEvent(p->st, p->gev[1 + b], 0));
+            if (c >= 1) {
+                // buffer 1 - b was last read by the adjoint sweep of segment c + 1
+                if (c + 1 < nseg) CK(cudaStreamWaitEvent(p->st2, p->gev[3 + (1 - b)], 0));
+                s = sweep(c - 1, 1 - b, nullptr, false, true);
+                if (s) return s;
+                CK(cudaEventRecord(p->gev[1 + (1 - b)], p->st2));
+            }
+            s = adjoint(c);
+            if (s) return s;
+            CK(cudaEventRecord(p->gev[3 + b], p->st));
+        }
+        // (the last recompute joined p->st before the last adjoint sweep)
     }
     CKL(launch_unpad_grad(gacc, grad_m, p->n[0], p->n[1], p->n[2], p->nzp, p->st));
     return WAVE_OK;
@@ -1239,7 +1339,7 @@ struct wave_batch_s {
     cudaGraphExec_t gexec = nullptr;
     std::vector<const float*> gobs;
     std::vector<float*> ggrad;
-    std::vector<int> gK;
+    std::vector<int> gK;  // per shot: segment length, and 1 << 30 when its adjoint sweep overlaps the recompute
     std::vector<unsigned long long> ggens;
     // persistent kernel of the forward graph: descriptors, tensor maps and
     // items of the work queue, and its counters [next, abort, err, pad,
@@ -1627,13 +1727,35 @@ extern "C" wave_status wave_batch_forward(wave_batch_t b, float* const* rec_out,
     return batch_run(b, b->exec, static_cast<cudaStream_t>(stream), b->persistent);
 }
 
+namespace {
+
+// Slab length of the persistent kernel's work items: 256 planes (or all of
+// x), so that the pipeline fill of an item (2 r T planes) costs little beside
+// its slab, while a pass level of the whole batch still has two items per SM
+// (counted with the one-step team tiles, 8 x 64 points, four to an item);
+// shorter slabs, down to 32 planes, for a batch too small for that.
+int batch_slab(wave_batch_t b)
+{
+    const long long want = 2LL * (b->plans.empty() ? 1 : b->plans[0]->sm_count);
+    for (int xc : {256, 128, 64}) {
+        long long items = 0;
+        for (auto* p : b->plans)
+            items += static_cast<long long>((p->n[0] + xc - 1) / xc) * ((p->n[1] + 7) / 8) * ((p->n[2] + 63) / 64) / 4;
+        if (items >= want) return xc;
+    }
+    return 32;
+}
+
+}  // namespace
+
 extern "C" wave_status wave_batch_autotune(wave_batch_t b, int passes)
 {
     if (!b || passes < 1) return fail(WAVE_ERR_ARG, "wave_batch_autotune: bad argument");
     DeviceGuard g(b->dev);
+    const int xc = batch_slab(b);
     for (auto* p : b->plans) {
         int count = 0;
-        wave_status s = autotune_impl(p, passes, 0, p->R == 2 || p->R == 4, nullptr, nullptr, 0, &count);
+        wave_status s = autotune_impl(p, passes, 0, (p->R == 2 || p->R == 4) ? xc : 0, nullptr, nullptr, 0, &count);
         if (s) return s;
     }
     return WAVE_OK;
@@ -1689,7 +1811,7 @@ extern "C" wave_status wave_batch_gradient(wave_batch_t b, const float* const* d
     for (size_t i = 0; i < n; ++i) {
         wave_status s = gradient_prepare(b->plans[i], checkpoint_every, &gps[i]);
         if (s) return s;
-        K[i] = gps[i].K;
+        K[i] = gps[i].K | (gps[i].pipe ? (1 << 30) : 0);
     }
     bool same = b->gexec && b->gK == K && b->ggens == batch_gens(b);
     for (size_t i = 0; same && i < n; ++i) same = b->gobs[i] == d_obs[i] && b->ggrad[i] == grad_m[i];

@@ -80,23 +80,6 @@ __global__ void rec_gather_kernel(const float* __restrict__ u, const int* __rest
 
 // grad -= scale * mu * (v_new - v_old), scale = 1/dt^2: the imaging condition
 // mu^{n+1} (u^{n+1} - 2u^n + u^{n-1}) / dt^2 with u^{n+1} - u^n = v^{n+1/2}.
-__global__ void grad_accum_kernel(float* __restrict__ grad, const float* __restrict__ mu,
-                                  const float* __restrict__ vn, const float* __restrict__ vo, long long n4, float scale)
-{
-    for (long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; p < n4;
-         p += static_cast<long long>(gridDim.x) * blockDim.x) {
-        float4 g = reinterpret_cast<float4*>(grad)[p];
-        const float4 m = reinterpret_cast<const float4*>(mu)[p];
-        const float4 a = reinterpret_cast<const float4*>(vn)[p];
-        const float4 b = reinterpret_cast<const float4*>(vo)[p];
-        g.x = __fmaf_rn(-__fmul_rn(scale, m.x), __fsub_rn(a.x, b.x), g.x);
-        g.y = __fmaf_rn(-__fmul_rn(scale, m.y), __fsub_rn(a.y, b.y), g.y);
-        g.z = __fmaf_rn(-__fmul_rn(scale, m.z), __fsub_rn(a.z, b.z), g.z);
-        g.w = __fmaf_rn(-__fmul_rn(scale, m.w), __fsub_rn(a.w, b.w), g.w);
-        reinterpret_cast<float4*>(grad)[p] = g;
-    }
-}
-
 __global__ void init_state_kernel(const float* __restrict__ u2, float* __restrict__ u, float* __restrict__ v, int nx,
                                   int ny, int nz, int nzp)
 {
@@ -234,14 +217,6 @@ cudaError_t launch_rec_reduce(const float* slots, const int* tptr, const float* 
     if (rows <= 0 || nrec <= 0) return cudaSuccess;
     rec_reduce_kernel<<<grid_for(static_cast<long long>(rows) * nrec, 256), 256, 0, st>>>(slots, tptr, tw, rec, rows,
                                                                                           nrec, ntaps);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_grad_accum(float* grad, const float* mu, const float* v_new, const float* v_old, long long n,
-                              float scale, cudaStream_t st)
-{
-    const long long n4 = n / 4;
-    grad_accum_kernel<<<grid_for(n4, 256), 256, 0, st>>>(grad, mu, v_new, v_old, n4, scale);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,14 @@ struct PassArgs {
     int nitems;
     int exch_nit;
     int* err;               // device error word (bit 0: a bounded wait gave up; bit 1: a tile waited too long for its neighbour)
+    // imaging condition of the FWI gradient, fused into a one-step adjoint
+    // pass (gacc == nullptr: none): at every point the pass writes,
+    // gacc += -(img_scale * mu) * (img_vn - img_vo), mu the adjoint field it
+    // wrote and img_vn - img_vo = v^{j-1/2} - v^{j-3/2} of the forward
+    float* gacc;
+    const float* img_vn;
+    const float* img_vo;
+    float img_scale;
 };
 
 // One compiled instantiation of the pass kernel: radius R, T steps, thread
@@ -125,9 +133,6 @@ cudaError_t launch_rec_reduce(const float* slots, const int* tptr, const float* 
 // launch_rec_reduce.
 cudaError_t launch_rec_gather(const float* u, const int* gidx, const int* tptr, const float* tw, float* rec, int nrec,
                               cudaStream_t st);
-// grad -= scale * mu * (v_new - v_old)   (scale = 1/dt^2)
-cudaError_t launch_grad_accum(float* grad, const float* mu, const float* v_new, const float* v_old, long long n,
-                              float scale, cudaStream_t st);
 cudaError_t launch_unpad_grad(const float* src, float* dst, int nx, int ny, int nz, int nzp, cudaStream_t st);
 cudaError_t launch_residual(const float* rec, const float* dobs, float* resid_rev, double* partial, int nt,
                             int nrec, cudaStream_t st);

@@ -6,7 +6,9 @@
   (receivers as sources, time-reversed residual) and matches the oracle;
 * adjoint traces and gradient vs the oracle's (relative L2);
 * the gradient does not depend on the checkpoint interval (bit-identical:
-  the recompute uses the one-step kernel, bit-identical to the tiled one);
+  the recompute uses the one-step kernel, bit-identical to the tiled one),
+  nor on the schedule (the recompute overlapped with the adjoint sweep, or
+  serial);
 * the gradient matches central finite differences of the FP64 oracle misfit
   at 16 seeded cells;
 * FWIGradient (torch.autograd.Function) returns the same gradient.
@@ -145,6 +147,31 @@ def test_gradient_vs_oracle_and_checkpointing(W, oracle):
         assert J2 == J
         assert np.array_equal(g2.cpu().numpy(), g), K
     plan.close()
+
+
+def test_gradient_overlapped_schedule_bit_identical(W, oracle, monkeypatch):
+    """The recompute of one segment on the plan's second stream, overlapped
+    with the adjoint sweep of the next (two segment buffers), gives the
+    serial schedule's misfit and gradient bit for bit, single and batched."""
+    P = problem(nt=50)
+    ok = oracle_kw(P)
+    d_obs, _, _ = oracle.forward(P["shape"], P["h"], P["so"], P["dt"], P["nt"], P["m_true"].astype(np.float64),
+                                 src_xyz=P["src"], wavelet=P["wav"], rec_xyz=P["rec"], **ok)
+    dobs_t = torch.from_numpy(d_obs.astype(np.float32)).cuda()
+    out = {}
+    for serial in ("1", "0"):
+        monkeypatch.setenv("WAVE_GRADIENT_SERIAL", serial)
+        plan = plan_for(W, P, P["m0"])
+        J, g = plan.gradient(dobs_t, checkpoint_every=6)
+        b = W.WaveBatch([plan])
+        Jb, gb = b.gradient([dobs_t], checkpoint_every=6)
+        out[serial] = (J, g.clone(), Jb[0], gb[0].clone())
+        b.close()
+        plan.close()
+    assert out["0"][0] == out["1"][0] == out["0"][2] == out["1"][2]
+    assert torch.equal(out["0"][1], out["1"][1])
+    assert torch.equal(out["0"][1], out["0"][3])
+    assert torch.equal(out["1"][1], out["1"][3])
 
 
 def test_gradient_central_differences_16_cells(W, oracle):
