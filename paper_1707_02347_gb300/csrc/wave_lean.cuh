@@ -234,7 +234,9 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, lean_min_
         // order, each into a slot the compute warps have released.  The
         // slot of iteration j of ring A is free once every compute warp has
         // finished iteration j - NA + r (its last read, as the centre plane);
-        // the slot of ring B once iteration j - NB is done.
+        // the slot of ring B once iteration j - NB is done.  The fields are
+        // the previous pass's outputs: copies start once it has completed.
+        grid_dep_wait();
         if (lane == 0) {
             int sa = 0, sb = 0, issued = 0;
             for (int j = 0; j < NIT; ++j) {
@@ -671,6 +673,8 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, lean_min_
             if (++sB == NB) { sB = 0; phB ^= 1; }
         };
 
+        // the outputs overwrite what the previous pass read: wait for it
+        grid_dep_wait();
         int i = 0;
         static_for<T>([&](auto kc) {
             constexpr int k = decltype(kc)::value;  // steps 0 .. k-1 active in this phase
@@ -681,6 +685,7 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, lean_min_
         __syncwarp();
         tmem_wait_st();
     }
+    grid_dep_launch();
     // every warp is done with the tensor memory (and the producer with its
     // copies) before warp 0 frees it
     tmem_fence_before();
@@ -703,8 +708,7 @@ cudaError_t launch_lean(const CUtensorMap& mapA, const CUtensorMap& mapV, const 
     auto fn = lean_kernel<R, T, QZ, RY, NY, SH>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    fn<<<static_cast<unsigned>(blocks), LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, smem, st>>>(mapA, mapV, mapK, a);
-    return cudaGetLastError();
+    return launch_dependent(fn, blocks, LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, smem, st, mapA, mapV, mapK, a);
 }
 
 }  // namespace detail

@@ -494,6 +494,41 @@ constexpr int min_blocks()
                                      : 1;
 }
 
+// Programmatic dependent launch of consecutive passes in a stream: a pass
+// lets the next one be scheduled once every one of its blocks has left its
+// plane loop (grid_dep_launch), and the next one runs its prologue (tensor
+// memory, mbarriers, tap lookups) on SMs that free up, then waits in
+// grid_dep_wait until the previous pass has completed and its writes are
+// visible, before it touches the fields.  Without the launch attribute both
+// are no-ops.
+__device__ __forceinline__ void grid_dep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch a pass kernel with programmatic stream serialisation allowed.
+template <class... P, class... A>
+cudaError_t launch_dependent(void (*fn)(P...), long long blocks, int threads, size_t smem, cudaStream_t st,
+                             A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, std::forward<A>(args)...);
+}
+
 __device__ __forceinline__ void mbar_inval(uint32_t bar)
 {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
@@ -940,8 +975,10 @@ __global__ void __launch_bounds__(QZ * RY, min_blocks<R, T, QZ, RY, QM>())
         tmem_fence_after();
         tbase = *s_tmem;
     }
+    grid_dep_wait();
     pass_tile<R, T, QZ, RY, QM>(&mapA, &mapV, &mapK, a, a.n0, blockIdx.x, smem, tbase, false,
                                 Team{static_cast<int>(threadIdx.x), 0, static_cast<int>(blockDim.x)});
+    grid_dep_launch();
     if constexpr (TQ) {
         if (threadIdx.x < 32) tmem_dealloc(tbase, TG::COLS);
     }
@@ -965,8 +1002,7 @@ cudaError_t launch_impl(const CUtensorMap& mapA, const CUtensorMap& mapV, const 
     auto fn = pass_kernel<R, T, QZ, RY, QM>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    fn<<<static_cast<unsigned>(blocks), threads, smem, st>>>(mapA, mapV, mapK, a);
-    return cudaGetLastError();
+    return launch_dependent(fn, blocks, threads, smem, st, mapA, mapV, mapK, a);
 }
 
 }  // namespace detail
