@@ -367,15 +367,6 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, lean_min_
         auto body = [&](int i, auto nact_c, auto out_c) {
             constexpr int NACT = decltype(nact_c)::value;
             constexpr bool OUTP = decltype(out_c)::value;
-            // (one-step adjoint pass of the gradient) the imaging operands of the plane this iteration writes
-            ImageIn img[NY];
-            const bool imaging = T == 1 && OUTP && a.gacc != nullptr;
-            if (imaging) {
-                const long long xo = static_cast<long long>(xbase + i - T * R) * a.sx;
-#pragma unroll
-                for (int r = 0; r < NY; ++r)
-                    if (own[r]) img[r] = image_load(a, xo + colofs[r]);
-            }
             // (SH) kappa of steps k >= 1 at their planes, fetched early (cache
             // hits); otherwise it comes down the delay line from step k-1
             float4 kpre[T][NY];
@@ -662,7 +653,8 @@ __global__ void __launch_bounds__(LeanGeo<R, T, QZ, RY, NY, SH>::NTHR, lean_min_
                     if (own[r]) {
                         *reinterpret_cast<float4*>(a.out_u + xo + colofs[r]) = pu[r];
                         *reinterpret_cast<float4*>(a.out_v + xo + colofs[r]) = pv[r];
-                        if (imaging) image_store(a, xo + colofs[r], img[r], pu[r]);
+                        if constexpr (T == 1)
+                            if (a.gacc != nullptr) image4(a, xo + colofs[r], pu[r]);
                     }
             }
             // advance the ring positions

@@ -539,30 +539,19 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar)
 // the adjoint field mu times dt^2 D_tt u of the forward, where
 // dt^2 D_tt u^{j-1} = v^{j-1/2} - v^{j-3/2}.  Each point is written by the
 // one thread that owns it in a one-step pass.
-// The operands are loaded at the start of the iteration that writes the
-// point (image_load), so that their latency overlaps the stencil.
-struct ImageIn {
-    float4 g, d;  // accumulator, and v_new - v_old
-};
-
-__device__ __forceinline__ ImageIn image_load(const PassArgs& a, long long off)
+// The operands are loaded where the point is written: loading them earlier
+// keeps their registers live through the stencil of every pass, which cost
+// the radius-8 pass registers and speed, and did not make the gradient faster.
+__device__ __forceinline__ void image4(const PassArgs& a, long long off, const float4& mu)
 {
-    ImageIn in;
-    in.g = *reinterpret_cast<const float4*>(a.gacc + off);
+    float4 g = *reinterpret_cast<const float4*>(a.gacc + off);
     const float4 vn = __ldg(reinterpret_cast<const float4*>(a.img_vn + off));
     const float4 vo = __ldg(reinterpret_cast<const float4*>(a.img_vo + off));
-    in.d = make_float4(__fsub_rn(vn.x, vo.x), __fsub_rn(vn.y, vo.y), __fsub_rn(vn.z, vo.z), __fsub_rn(vn.w, vo.w));
-    return in;
-}
-
-__device__ __forceinline__ void image_store(const PassArgs& a, long long off, const ImageIn& in, const float4& mu)
-{
     const float s = a.img_scale;
-    float4 g = in.g;
-    g.x = __fmaf_rn(-__fmul_rn(s, mu.x), in.d.x, g.x);
-    g.y = __fmaf_rn(-__fmul_rn(s, mu.y), in.d.y, g.y);
-    g.z = __fmaf_rn(-__fmul_rn(s, mu.z), in.d.z, g.z);
-    g.w = __fmaf_rn(-__fmul_rn(s, mu.w), in.d.w, g.w);
+    g.x = __fmaf_rn(-__fmul_rn(s, mu.x), __fsub_rn(vn.x, vo.x), g.x);
+    g.y = __fmaf_rn(-__fmul_rn(s, mu.y), __fsub_rn(vn.y, vo.y), g.y);
+    g.z = __fmaf_rn(-__fmul_rn(s, mu.z), __fsub_rn(vn.z, vo.z), g.z);
+    g.w = __fmaf_rn(-__fmul_rn(s, mu.w), __fsub_rn(vn.w, vo.w), g.w);
     *reinterpret_cast<float4*>(a.gacc + off) = g;
 }
 
@@ -744,10 +733,6 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap* mapA, const CUtenso
         constexpr bool MOVE = !TQ && SR < 0;
         (void)S;
         (void)MOVE;
-        // (one-step adjoint pass of the gradient) the imaging operands of the plane this iteration writes
-        ImageIn img{};
-        const bool imaging = T == 1 && OUTP && own && a.gacc != nullptr;
-        if (imaging) img = image_load(a, (xbase + i - T * R) * sx + colofs);
         // kappa of steps k >= 1 at their planes, fetched early (cache hits)
         float4 kpre[T];
 #pragma unroll
@@ -908,7 +893,8 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap* mapA, const CUtenso
             const long long off = (xbase + i - T * R) * sx + colofs;
             *reinterpret_cast<float4*>(a.out_u + off) = prev_u;
             *reinterpret_cast<float4*>(a.out_v + off) = prev_v;
-            if (imaging) image_store(a, off, img, prev_u);
+            if constexpr (T == 1)
+                if (a.gacc != nullptr) image4(a, off, prev_u);
         }
         // advance the ring positions
         vslot = vslot == NV - 1 ? 0 : vslot + 1;
