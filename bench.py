@@ -151,7 +151,7 @@ def kernel_traffic(T, so=8, variant=2, key="dram_bytes_per_point"):
     for f in kernel_sources(variant):
         sha.update(open(os.path.join(ROOT, "paper_1707_02347_gb300", "csrc", f), "rb").read())
     h = sha.hexdigest()[:16]
-    name = {8: "tiled_pass_so8_512.md", 16: "tiled_pass_so16_768.md"}.get(so)
+    name = {4: "tiled_pass_so4_512.md", 8: "tiled_pass_so8_512.md", 16: "tiled_pass_so16_768.md"}.get(so)
     if name is None:
         return None, h
     path = os.path.join(ROOT, "profiles", name)
