@@ -233,7 +233,9 @@ wave_status wave_adjoint(wave_plan_t plan, const float* rec_resid, float* src_ou
  * the plan while the adjoint steps through the next).  K = 0 (or K >= nt)
  * keeps every increment of one forward sweep when it fits in device memory,
  * with no recomputation.  The imaging condition is fused into the adjoint
- * passes.  The result does not depend on K. */
+ * passes.  The result does not depend on K.  The environment variable
+ * WAVE_GRADIENT_SERIAL=1 keeps one segment buffer and one stream (the same
+ * bits, less memory, slower). */
 wave_status wave_gradient(wave_plan_t plan, const float* d_obs, float* grad_m, double* misfit,
                           int checkpoint_every);
 
