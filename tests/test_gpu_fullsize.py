@@ -1,8 +1,9 @@
 """Parity at the full sizes, in the launch configurations the benchmark
 times: the 512^3 SO8 workload (the warp-specialised one-step pass the
-autotuner picks, and the T = 2 pass with the x queues in tensor memory) and
-the 768 x 768 x 384 SO16 workload with its 501 x 501 receiver surface (the
-warp-specialised one-step pass with two rows per thread).
+autotuner picks, and the T = 2 pass with the x queues in tensor memory), the
+same grid at SO4 (the warp-specialised two-step pass the autotuner picks
+there), and the 768 x 768 x 384 SO16 workload with its 501 x 501 receiver
+surface (the warp-specialised one-step pass with two rows per thread).
 
 The other variants (the block-barrier one-step pass, the skewed wavefront
 and warp-specialised two-step passes, the one-row SO16 pass) are checked
@@ -136,6 +137,48 @@ def test_full_size_two_one_step_passes_equal_one_t2_pass(state):
 def test_full_size_one_step_variants_bit_identical(state):
     _, _, out = state
     assert np.array_equal(out[1], out["T1v2"])  # warp-specialised vs block-barrier one-step pass
+
+
+@pytest.fixture(scope="module")
+def state4(oracle):
+    """512^3 SO4: N1 steps, then two more steps from that state as one
+    two-step pass in the launch configuration the SO4 bench picks (40 x 56
+    tile, 64-plane slabs, warp-specialised pass) and as two one-step passes."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1707_02347_gb300 as W
+    from paper_1707_02347_gb300 import inputs
+
+    W.load()
+    dev = torch.device("cuda")
+    w = inputs.layered_forward((N, N, N), 4, N1 + 2, seed=1, f=15.0, h=10.0, sponge_width=10, nrec_line=512)
+    m = torch.from_numpy(np.ascontiguousarray(w.m)).to(dev)
+    wav = np.ascontiguousarray(w.wavelet.astype(np.float32))
+    kw = dict(sponge_width=w.sponge_width, vmax=w.vmax)
+    plan = W.WavePlan(w.shape, w.spacing, 4, w.dt, N1, m, tiling=(1, 8, 64, 64, 5), **kw)
+    plan.set_sources(w.src_xyz, torch.from_numpy(wav[:N1]).to(dev))
+    plan.set_receivers(w.rec_xyz)
+    _, uA = plan.forward(want_final=True)
+    plan.close()
+    out = {}
+    for name, tiling in (("T2", (2, 40, 56, 64, 5)), ("T1x2", (1, 8, 64, 64, 5))):
+        p = W.WavePlan(w.shape, w.spacing, 4, w.dt, 2, m, tiling=tiling, **kw)
+        p.set_sources(w.src_xyz, torch.from_numpy(wav[N1:N1 + 2].copy()).to(dev))
+        _, uB = p.forward(u_init=uA, want_final=True)
+        torch.cuda.synchronize()
+        out[name] = uB[1].cpu().numpy()
+        p.close()
+    return w, uA.cpu().numpy(), out
+
+
+def test_full_size_so4_two_step_pass_vs_oracle_at_sampled_points(state4, oracle):
+    w, A, out = state4
+    _check_sampled(oracle, w, A, out["T2"], 2, 44)
+
+
+def test_full_size_so4_two_step_pass_equals_two_one_step_passes(state4):
+    _, _, out = state4
+    assert np.array_equal(out["T2"], out["T1x2"])
 
 
 N1_16 = 100  # SO16 steps before the checked pass (the Ricker peaks near step 66)
